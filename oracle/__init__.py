@@ -1,0 +1,5 @@
+"""CPU oracle for the CUBICS hot path (test infrastructure only).
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's CPU baseline leg may import this
+package.  It shares no code with the CUDA library.
+"""
