@@ -1,0 +1,197 @@
+/*
+ * cubics.h — C ABI of the GB300 CUBICS hot path (arxiv 1909.09213).
+ *
+ * A problem is the CSP triple (X, D, C) of Section 1.1: `csp_create` makes the variables X
+ * with their domains D, `csp_remove_value` cuts arbitrary holes in D, and the `csp_post_*`
+ * calls add the constraints C.  The host builds and encodes the problem and moves it to the
+ * GPU once; labeling, propagation and backtracking then run entirely on the device, and
+ * only solutions and statistics come back (Section 2.1).
+ *
+ * Conventions shared by every call:
+ *   - every function returns an int status (CSP_OK or a negative CSP_E* code); on error the
+ *     handle is unchanged;
+ *   - pointers named `host` point to host memory, `dev` to device memory; the library copies
+ *     host arrays it is given and never keeps or frees caller pointers;
+ *   - the library never allocates device memory: the caller binds a device workspace of
+ *     `csp_workspace_bytes` bytes (e.g. a torch.uint8 CUDA tensor) and a CUDA stream;
+ *   - handles are not thread-safe; there is no CPU fallback: without a usable GPU every
+ *     device call returns CSP_ECUDA.
+ *
+ * Domains on the device are bitsets: all variables of one problem share the window
+ * lo0 .. lo0 + 32*W - 1 (lo0 = min lo_i, W = ceil(span/32) words, span <= 256), and bit k of a
+ * domain stands for the value lo0 + k.  `csp_layout` reports n, W and lo0.
+ */
+#ifndef CUBICS_H
+#define CUBICS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CSP_OK = 0,
+    CSP_EINVAL = -1,    /* bad argument: variable index, empty domain, x == y table, ... */
+    CSP_ENOMEM = -2,    /* bound workspace smaller than csp_workspace_bytes */
+    CSP_ETOOBIG = -3,   /* beyond the supported sizes (n > 1024, span > 256, overflow risk) */
+    CSP_ECUDA = -4,     /* CUDA error or no device */
+    CSP_ELIMIT = -5,    /* node or time limit reached; statistics are partial */
+    CSP_ETIMEOUT = -6,  /* a device-side wait for work exceeded wait_limit_ns */
+    CSP_ESTATE = -7     /* call out of order (e.g. solve before bind) */
+};
+
+enum { CSP_ALL = 0, CSP_FIRST = 1, CSP_PROPAGATE = 2 };
+enum { CSP_BR_FIRST_FAIL = 0, CSP_BR_LEARNED = 1 };
+
+/* test hook flags for csp_limits.flags */
+enum { CSP_F_NO_DONATE = 1 };   /* workers never share subtrees (exercises the wait limit) */
+
+typedef struct csp csp_t;
+typedef struct csp_batch csp_batch_t;
+
+typedef struct {
+    int64_t node_limit;      /* stop after about this many nodes; 0 = none */
+    int64_t time_limit_ns;   /* stop after this device time; 0 = none */
+    int64_t wait_limit_ns;   /* bound on every device-side wait; 0 = 60 s */
+    int32_t flags;           /* CSP_F_* */
+    int32_t reserved;
+} csp_limits;
+
+/* Launch shape of the search kernel.  0 fields are chosen by the library. */
+typedef struct {
+    int32_t blocks;           /* persistent blocks; 0 = resident blocks on every SM */
+    int32_t warps_per_block;  /* workers per block (one warp each) */
+    int32_t smem_levels;      /* search-stack levels kept in shared memory per worker */
+    int32_t queue_records;    /* capacity of each work queue (power of two) */
+} csp_tiling;
+
+typedef struct {
+    uint64_t nodes;          /* fixpoint calls, root included */
+    uint64_t fails;          /* fixpoint calls that emptied a domain */
+    uint64_t solutions;      /* all solutions (CSP_ALL) or 1/0 (CSP_FIRST) */
+    uint64_t sol_hash_sum;   /* sum over solutions of the solution hash (mod 2^64) */
+    uint64_t sol_hash_xor;   /* xor over solutions of the solution hash */
+    uint64_t prop_evals;     /* propagator evaluations */
+    uint64_t steals;         /* subtrees handed from one worker to another */
+    uint64_t spills;         /* search-stack levels moved from shared to global memory */
+    int32_t max_depth;       /* deepest open search level seen */
+    int32_t status;          /* last call's status */
+    double ms;               /* device time of the last search launch */
+    int64_t stored;          /* solutions written to sol_out */
+    int32_t workers;         /* workers (warps) of the last launch */
+    int32_t blocks;          /* blocks of the last launch */
+} csp_stats_t;
+
+typedef struct {
+    int32_t status;          /* 1 SAT, 0 UNSAT, < 0 error (CSP_ELIMIT, ...) */
+    int32_t n;               /* number of variables */
+    uint64_t nodes;          /* nodes spent on this instance */
+    uint64_t fails;
+    uint64_t solutions;      /* CSP_ALL: every solution; CSP_FIRST: 1 when SAT */
+    int64_t sol_offset;      /* first solution of the instance: values at sol + sol_offset */
+} csp_result;
+
+/* ---------------------------------------------------------------- model (host only) */
+
+/* Create X = {x_0..x_{n-1}} with D_i = {lo[i]..hi[i]} (Section 1.1).  Every hi[i] - lo[i]
+ * must be in 0..255 and all values must fit one window of 256 consecutive integers.
+ * lo, hi: host arrays of n_vars entries.  Returns CSP_EINVAL for n_vars < 1 or hi < lo,
+ * CSP_ETOOBIG for n_vars > 1024 or a window wider than 256. */
+int csp_create(csp_t **out, int32_t n_vars, const int32_t *lo, const int32_t *hi);
+
+/* Remove `value` from D_var (arbitrary finite domains, Section 1.1).  Values outside the
+ * domain are ignored.  CSP_EINVAL for a bad index. */
+int csp_remove_value(csp_t *h, int32_t var, int32_t value);
+
+/* x != y + c; y < 0 posts the unary x != c.  Propagation: when one side is fixed, the value
+ * it forbids is removed from the other (Section 1.1, "constraints propagation"). */
+int csp_post_int_ne(csp_t *h, int32_t x, int32_t y, int32_t c);
+
+/* sum_{t<k} coef[t] * x_{vars[t]} <= rhs, bounds-consistent.  Repeated variables are merged
+ * and zero coefficients dropped.  coef, vars: host arrays of k entries.  CSP_ETOOBIG when
+ * sum |coef| * max |value| + |rhs| could exceed 2^30. */
+int csp_post_int_lin_le(csp_t *h, int32_t k, const int32_t *coef, const int32_t *vars,
+                        int32_t rhs);
+
+/* all different over k distinct variables: fixed values are removed from the other
+ * members; fails when two members share a fixed value or when fewer than k values remain
+ * in the union of their domains.  vars: host array of k entries; repeats are CSP_EINVAL. */
+int csp_post_alldiff(csp_t *h, int32_t k, const int32_t *vars);
+
+/* Binary relation as a tuple set (c2 of Section 1.1), arc-consistent.  allowed: host array
+ * of (hi_x - lo_x + 1) rows of row_words uint32 words; bit b of row a allows the pair
+ * (lo_x + a, lo_y + b).  row_words >= ceil((hi_y - lo_y + 1) / 32).  x == y is CSP_EINVAL. */
+int csp_post_table(csp_t *h, int32_t x, int32_t y, const uint32_t *allowed, int32_t row_words);
+
+/* Device domain layout: n variables, W uint32 words per domain, bit k = value lo0 + k. */
+int csp_layout(const csp_t *h, int32_t *n, int32_t *W, int32_t *lo0);
+
+/* ---------------------------------------------------------------- device (single problem) */
+
+/* Launch shape; NULL or zero fields restore the library's choice.  Changes the workspace
+ * size. */
+int csp_set_tiling(csp_t *h, const csp_tiling *t);
+
+/* Bytes of device workspace needed for `mode` (CSP_ALL / CSP_FIRST with up to `cap` stored
+ * solutions, or CSP_PROPAGATE with cap = number of domain states) under the current tiling. */
+int csp_workspace_bytes(const csp_t *h, int32_t mode, int64_t cap, size_t *bytes);
+
+/* Bind a device workspace (dev, >= csp_workspace_bytes, 256-byte aligned) and a CUDA stream
+ * (cudaStream_t as void*, NULL = legacy default stream).  The caller owns both and must keep
+ * them alive until the handle is destroyed or rebound. */
+int csp_bind(csp_t *h, void *dev, size_t bytes, void *cuda_stream);
+
+/* Branching heuristic: CSP_BR_FIRST_FAIL (smallest domain, lowest index) or
+ * CSP_BR_LEARNED with the brancher's bf16 weights (host array, csp_brancher_params()
+ * values; NULL keeps the loaded weights).  Learned ordering changes only exploration order. */
+int csp_set_brancher(csp_t *h, int32_t kind, const uint16_t *bf16_weights);
+
+/* Search (Sections 1.1 and 2.1): d-way branching on the chosen variable, values ascending,
+ * every node propagated to its fixpoint on the GPU, backtracking on device.  CSP_ALL counts
+ * every solution and stores up to cap of them (any `cap` of them, unordered); CSP_FIRST stops
+ * at the first.  sol_out: host array of cap * n int32 values (may be NULL when cap == 0).
+ * Encodes and uploads the problem, launches, waits, and copies results back.  lim may be NULL. */
+int csp_solve(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out, const csp_limits *lim);
+
+/* The device part of csp_solve alone: requires a previous csp_solve or csp_upload with the
+ * same mode and cap; enqueues the search on the bound stream and returns without waiting.
+ * Results stay in the workspace until csp_collect. */
+int csp_upload(csp_t *h, int32_t mode, int64_t cap);
+int csp_launch(csp_t *h, const csp_limits *lim);
+int csp_collect(csp_t *h, int32_t *sol_out);
+
+/* One fixpoint per domain state (test hook; Section 1.1 "constraints propagation").
+ * dom_in, dom_out: host arrays of count * n * W words (layout of csp_layout); failed: host
+ * array of count int32 (1 = some domain became empty; dom_out is then unspecified). */
+int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom_out,
+                  int32_t *failed);
+
+int csp_stats(const csp_t *h, csp_stats_t *out);
+void csp_destroy(csp_t *h);
+const char *csp_strerror(int code);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Many problems solved by one persistent launch: each block takes the next instance from an
+ * atomic ticket and its warps share that instance's subtrees.  The handles must outlive the
+ * batch; their models are encoded at csp_batch_create. */
+int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count);
+int csp_batch_set_tiling(csp_batch_t *b, const csp_tiling *t);
+int csp_batch_workspace_bytes(const csp_batch_t *b, int32_t mode, size_t *bytes);
+int csp_batch_bind(csp_batch_t *b, void *dev, size_t bytes, void *cuda_stream);
+/* out: host array of count results; sol: host array of csp_batch_solution_words() int32
+ * (first solution per SAT instance), may be NULL.  use_graph != 0 replays a CUDA graph. */
+int csp_batch_solve(csp_batch_t *b, int32_t mode, const csp_limits *lim, int32_t use_graph,
+                    csp_result *out, int32_t *sol);
+int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph);
+int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol);
+int64_t csp_batch_solution_words(const csp_batch_t *b);
+int csp_batch_stats(const csp_batch_t *b, csp_stats_t *out);
+void csp_batch_destroy(csp_batch_t *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUBICS_H */

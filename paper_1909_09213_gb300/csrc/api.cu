@@ -1,0 +1,922 @@
+// Host side of the CUBICS C ABI: model building and validation, encoding into the device
+// layout of internal.h, workspace carving, and kernel launches (arxiv 1909.09213,
+// Section 2.1: the CPU builds the data structures and moves them to the GPU, control then
+// stays on the GPU until the results come back).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "../../include/cubics.h"
+#include "internal.h"
+
+namespace cubics {
+cudaError_t launch_search(int W, const SearchArgs &A, int blocks, int threads, size_t smem,
+                          cudaStream_t st);
+cudaError_t occupancy_search(int W, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t set_search_smem(int W, size_t smem);
+cudaError_t launch_init_single(const SearchArgs &A, cudaStream_t st);
+cudaError_t launch_init_batch(const SearchArgs &A, int teams, cudaStream_t st);
+cudaError_t launch_propagate(int W, const PropArgs &P, int blocks, int threads, size_t smem,
+                             cudaStream_t st);
+}  // namespace cubics
+
+using namespace cubics;
+
+namespace {
+
+constexpr size_t SMEM_MAX = 232448;          // 227 KB dynamic shared memory per block
+constexpr size_t ALIGN = 256;
+constexpr int64_t BOUND_LIMIT = int64_t(1) << 30;
+
+struct LinRow { std::vector<int32_t> coef, var; int32_t rhs; };
+struct Table { int32_t x, y; std::vector<uint8_t> allowed; };   // size_x * size_y flags
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int natural_w(int span) {
+    const int w = (span + 31) / 32;
+    return w <= 1 ? 1 : w <= 2 ? 2 : w <= 4 ? 4 : 8;
+}
+
+struct DeviceInfo {
+    int sms = 0;
+    bool ok = false;
+};
+
+DeviceInfo device_info() {
+    DeviceInfo d;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return d; }
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return d;
+    }
+    d.ok = true;
+    return d;
+}
+
+struct Shape {
+    int blocks = 0, warps = 0, lsm = 0, qcap = 0, stage_words = 0;
+    size_t smem = 0;
+};
+
+// Resources of one search launch.  R and depth are record words and stack levels per
+// worker, cons the words of constraint data to stage in shared memory.
+int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batch, Shape *s) {
+    s->warps = t.warps_per_block > 0 ? t.warps_per_block : 8;
+    if (s->warps > 32) return CSP_EINVAL;
+    int lsm = t.smem_levels > 0 ? t.smem_levels : std::max(2, 6144 / R);
+    lsm = std::max(2, std::min(lsm, depth));
+    const int cons4 = (cons + 3) & ~3;
+    size_t smem = (size_t)s->warps * (lsm * R + WS_WORDS) * 4;
+    while (smem > SMEM_MAX && lsm > 2) {
+        lsm--;
+        smem = (size_t)s->warps * (lsm * R + WS_WORDS) * 4;
+    }
+    if (smem > SMEM_MAX) return CSP_ETOOBIG;
+    s->stage_words = (smem + (size_t)cons4 * 4 <= SMEM_MAX) ? cons4 : 0;
+    s->smem = smem + (size_t)s->stage_words * 4;
+    s->lsm = lsm;
+    int q = t.queue_records > 0 ? t.queue_records : (batch ? 64 : 4096);
+    if (q & (q - 1)) return CSP_EINVAL;
+    s->qcap = q;
+    if (t.blocks > 0) {
+        s->blocks = t.blocks;
+    } else {
+        DeviceInfo di = device_info();
+        if (!di.ok) return CSP_ECUDA;
+        int bps = 0;
+        if (occupancy_search(W, s->warps * 32, s->smem, &bps) != cudaSuccess || bps < 1) {
+            cudaGetLastError();
+            return CSP_ECUDA;
+        }
+        s->blocks = di.sms * bps;
+    }
+    return CSP_OK;
+}
+
+// carve consecutive 256-byte aligned regions
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, ALIGN);
+        return o;
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- handle
+
+struct csp {
+    int32_t n = 0;
+    std::vector<int32_t> lo, hi;
+    std::vector<std::vector<uint8_t>> present;       // per var, flags over lo..hi
+    std::vector<int32_t> ne_x, ne_y, ne_c;
+    std::vector<LinRow> lin;
+    std::vector<std::vector<int32_t>> ad;
+    std::vector<Table> tab;
+    int32_t lo0 = 0, W = 1;
+    csp_tiling tiling{0, 0, 0, 0};
+    int32_t brancher = CSP_BR_FIRST_FAIL;
+    // device binding
+    uint8_t *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // last upload
+    bool uploaded = false;
+    int32_t up_mode = -1;
+    int64_t up_cap = 0;
+    std::vector<uint32_t> block;
+    Shape shape;
+    size_t o_inst = 0, o_off = 0, o_g = 0, o_team = 0, o_qseq = 0, o_qrec = 0, o_spill = 0,
+           o_sols = 0;
+    int R = 0, depth = 0;
+    csp_stats_t stats{};
+};
+
+namespace {
+
+int var_ok(const csp *h, int32_t v) { return h && v >= 0 && v < h->n; }
+
+void invalidate(csp *h) { h->uploaded = false; }
+
+// Encode the model with W words per domain (W >= the model's own W).
+void encode(const csp *h, int W, std::vector<uint32_t> &B) {
+    const int n = h->n, S = n * W, NW = (n + 31) / 32;
+    const int lo0 = h->lo0;
+    const int span = 32 * W;
+    B.assign(HDR_WORDS, 0u);
+    auto put = [&](uint32_t v) { B.push_back(v); };
+    auto align4 = [&]() { while (B.size() & 3) B.push_back(0u); };
+    uint32_t flags = 0;
+    // unary ne
+    std::vector<uint32_t> un;
+    std::vector<std::vector<uint32_t>> adj(n);
+    size_t n_ne = 0;
+    for (size_t k = 0; k < h->ne_x.size(); ++k) {
+        const int x = h->ne_x[k], y = h->ne_y[k];
+        const int64_t c = h->ne_c[k];
+        n_ne++;
+        if (y < 0) {
+            const int64_t bit = c - lo0;
+            if (bit >= 0 && bit < span) un.push_back((uint32_t)x | ((uint32_t)bit << 16));
+        } else if (c > -span && c < span) {
+            adj[y].push_back((uint32_t)x | ((uint32_t)(uint16_t)(int16_t)c << 16));
+            adj[x].push_back((uint32_t)y | ((uint32_t)(uint16_t)(int16_t)(-c) << 16));
+        }
+    }
+    B[H_N] = n; B[H_W] = W; B[H_LO0] = (uint32_t)lo0; B[H_S] = S; B[H_NW] = NW;
+    B[H_N_NE] = (uint32_t)n_ne;
+    B[H_N_UN] = (uint32_t)un.size();
+    B[H_OFF_UN] = (uint32_t)B.size();
+    for (uint32_t u : un) put(u);
+    B[H_OFF_ADJ_START] = (uint32_t)B.size();
+    uint32_t acc = 0;
+    for (int v = 0; v < n; ++v) { put(acc); acc += (uint32_t)adj[v].size(); }
+    put(acc);
+    B[H_OFF_ADJ] = (uint32_t)B.size();
+    for (int v = 0; v < n; ++v) for (uint32_t e : adj[v]) put(e);
+    // lin rows (already merged at post time)
+    const int nl = (int)h->lin.size();
+    B[H_N_LIN] = nl;
+    B[H_OFF_LIN_ROW] = (uint32_t)B.size();
+    uint32_t t0 = 0;
+    for (const LinRow &r : h->lin) {
+        put(t0); put((uint32_t)r.coef.size()); put((uint32_t)r.rhs);
+        t0 += (uint32_t)r.coef.size();
+        if (r.coef.empty() && r.rhs < 0) flags |= FLAG_TRIVIAL_FAIL;
+    }
+    B[H_OFF_LIN_TERM] = (uint32_t)B.size();
+    for (const LinRow &r : h->lin)
+        for (size_t t = 0; t < r.coef.size(); ++t) { put((uint32_t)r.coef[t]); put((uint32_t)r.var[t]); }
+    const int lmw = (nl + 31) / 32;
+    B[H_LIN_MW] = lmw;
+    B[H_OFF_LIN_MASK] = (uint32_t)B.size();
+    {
+        std::vector<uint32_t> m((size_t)n * lmw, 0u);
+        for (int r = 0; r < nl; ++r)
+            for (int32_t v : h->lin[r].var) m[(size_t)v * lmw + r / 32] |= 1u << (r % 32);
+        for (uint32_t w : m) put(w);
+    }
+    // alldiff
+    const int na = (int)h->ad.size();
+    B[H_N_AD] = na;
+    B[H_OFF_AD_ROW] = (uint32_t)B.size();
+    uint32_t m0 = 0;
+    for (const auto &g : h->ad) { put(m0); put((uint32_t)g.size()); m0 += (uint32_t)g.size(); }
+    B[H_OFF_AD_MEM] = (uint32_t)B.size();
+    for (const auto &g : h->ad) for (int32_t v : g) put((uint32_t)v);
+    const int amw = (na + 31) / 32;
+    B[H_AD_MW] = amw;
+    B[H_OFF_AD_MASK] = (uint32_t)B.size();
+    {
+        std::vector<uint32_t> m((size_t)n * amw, 0u);
+        for (int g = 0; g < na; ++g)
+            for (int32_t v : h->ad[g]) m[(size_t)v * amw + g / 32] |= 1u << (g % 32);
+        for (uint32_t w : m) put(w);
+    }
+    // tables: 4-word entries, then the R/C matrices (32*W rows of W words each)
+    const int nt = (int)h->tab.size();
+    B[H_N_TAB] = nt;
+    B[H_OFF_TAB] = (uint32_t)B.size();
+    const size_t tab_hdr = B.size();
+    for (int t = 0; t < nt; ++t) { put(0); put(0); put(0); put(0); }
+    for (int t = 0; t < nt; ++t) {
+        const Table &T = h->tab[t];
+        const int sx = h->hi[T.x] - h->lo[T.x] + 1, sy = h->hi[T.y] - h->lo[T.y] + 1;
+        const int ox = h->lo[T.x] - lo0, oy = h->lo[T.y] - lo0;
+        align4();
+        const size_t offR = B.size();
+        B.resize(offR + (size_t)2 * span * W, 0u);
+        const size_t offC = offR + (size_t)span * W;
+        for (int a = 0; a < sx; ++a)
+            for (int b = 0; b < sy; ++b)
+                if (T.allowed[(size_t)a * sy + b]) {
+                    const int ba = ox + a, bb = oy + b;
+                    B[offR + (size_t)ba * W + bb / 32] |= 1u << (bb % 32);
+                    B[offC + (size_t)bb * W + ba / 32] |= 1u << (ba % 32);
+                }
+        B[tab_hdr + 4 * t] = (uint32_t)T.x;
+        B[tab_hdr + 4 * t + 1] = (uint32_t)T.y;
+        B[tab_hdr + 4 * t + 2] = (uint32_t)offR;
+        B[tab_hdr + 4 * t + 3] = (uint32_t)offC;
+    }
+    align4();
+    B[H_CONS_WORDS] = (uint32_t)B.size();
+    B[H_OFF_ROOT] = (uint32_t)B.size();
+    const size_t root = B.size();
+    B.resize(root + (size_t)S, 0u);
+    for (int i = 0; i < n; ++i) {
+        const int o = h->lo[i] - lo0;
+        for (int k = 0; k <= h->hi[i] - h->lo[i]; ++k)
+            if (h->present[i][k]) B[root + (size_t)i * W + (o + k) / 32] |= 1u << ((o + k) % 32);
+    }
+    while (B.size() & 63) B.push_back(0u);
+    B[H_TOTAL] = (uint32_t)B.size();
+    B[H_R] = (uint32_t)record_words(S, W);
+    B[H_FLAGS] = flags;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return CSP_OK;
+    cudaGetLastError();
+    return CSP_ECUDA;
+}
+
+// Layout of a single-problem workspace for mode/cap under the current tiling.
+int plan_single(csp *h, int32_t mode, int64_t cap, size_t *bytes, std::vector<uint32_t> *blk) {
+    std::vector<uint32_t> local;
+    std::vector<uint32_t> &B = blk ? *blk : local;
+    encode(h, h->W, B);
+    Carver c;
+    h->o_inst = c.take(B.size() * 4);
+    h->o_off = c.take(sizeof(int64_t));
+    if (mode == CSP_PROPAGATE) {
+        const size_t sw = (size_t)h->n * h->W * 4;
+        h->o_qseq = c.take(sw * (size_t)cap);     // dom_in
+        h->o_qrec = c.take(sw * (size_t)cap);     // dom_out
+        h->o_sols = c.take(4 * (size_t)cap);      // failed
+        *bytes = c.off;
+        return CSP_OK;
+    }
+    const int R = record_words(h->n * h->W, h->W);
+    const int depth = h->n + 1;
+    Shape s;
+    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, &s);
+    if (rc) return rc;
+    h->shape = s;
+    h->R = R;
+    h->depth = depth;
+    h->o_g = c.take(sizeof(GState));
+    h->o_team = c.take(sizeof(Team));
+    h->o_qseq = c.take((size_t)s.qcap * 4);
+    h->o_qrec = c.take((size_t)s.qcap * R * 4);
+    h->o_spill = c.take((size_t)s.blocks * s.warps * depth * R * 4);
+    h->o_sols = c.take((size_t)std::max<int64_t>(cap, 1) * h->n * 4);
+    *bytes = c.off;
+    return CSP_OK;
+}
+
+SearchArgs single_args(csp *h, int32_t mode, int64_t cap, const csp_limits *lim) {
+    SearchArgs A{};
+    uint8_t *w = h->ws;
+    A.arena = (const uint32_t *)(w + h->o_inst);
+    A.inst_off = (const int64_t *)(w + h->o_off);
+    A.sol_off = nullptr;
+    A.n_inst = 1;
+    A.mode = mode;
+    A.batch = 0;
+    A.lsm = h->shape.lsm;
+    A.rmax = h->R;
+    A.depth = h->depth;
+    A.stage_words = h->shape.stage_words;
+    A.qmask = h->shape.qcap - 1;
+    A.flags = lim ? lim->flags : 0;
+    A.warps = h->shape.warps;
+    A.g = (GState *)(w + h->o_g);
+    A.teams = (Team *)(w + h->o_team);
+    A.qseq = (uint32_t *)(w + h->o_qseq);
+    A.qrec = (uint32_t *)(w + h->o_qrec);
+    A.spill = (uint32_t *)(w + h->o_spill);
+    A.sols = (int32_t *)(w + h->o_sols);
+    A.cap = mode == CSP_FIRST ? 1 : cap;
+    A.results = nullptr;
+    A.node_limit = lim ? lim->node_limit : 0;
+    A.deadline_ns = lim ? lim->time_limit_ns : 0;
+    A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
+    A.mlp = nullptr;
+    return A;
+}
+
+void fill_stats(csp_stats_t *s, const GState &g, int64_t stored) {
+    s->nodes = g.nodes;
+    s->fails = g.fails;
+    s->solutions = g.solutions;
+    s->sol_hash_sum = g.hsum;
+    s->sol_hash_xor = g.hxor;
+    s->prop_evals = g.evals;
+    s->steals = g.steals;
+    s->spills = g.spills;
+    s->max_depth = g.max_depth;
+    s->stored = stored;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- model calls
+
+extern "C" {
+
+int csp_create(csp_t **out, int32_t n_vars, const int32_t *lo, const int32_t *hi) {
+    if (!out || !lo || !hi || n_vars < 1) return CSP_EINVAL;
+    if (n_vars > MAX_VARS) return CSP_ETOOBIG;
+    int64_t mn = INT32_MAX, mx = INT32_MIN;
+    for (int i = 0; i < n_vars; ++i) {
+        if (hi[i] < lo[i]) return CSP_EINVAL;
+        mn = std::min<int64_t>(mn, lo[i]);
+        mx = std::max<int64_t>(mx, hi[i]);
+    }
+    if (mx - mn + 1 > 256) return CSP_ETOOBIG;
+    csp *h = new csp();
+    h->n = n_vars;
+    h->lo.assign(lo, lo + n_vars);
+    h->hi.assign(hi, hi + n_vars);
+    h->present.resize(n_vars);
+    for (int i = 0; i < n_vars; ++i) h->present[i].assign((size_t)(hi[i] - lo[i] + 1), 1);
+    h->lo0 = (int32_t)mn;
+    h->W = natural_w((int)(mx - mn + 1));
+    *out = h;
+    return CSP_OK;
+}
+
+int csp_remove_value(csp_t *h, int32_t var, int32_t value) {
+    if (!var_ok(h, var)) return CSP_EINVAL;
+    if (value >= h->lo[var] && value <= h->hi[var]) h->present[var][value - h->lo[var]] = 0;
+    invalidate(h);
+    return CSP_OK;
+}
+
+int csp_post_int_ne(csp_t *h, int32_t x, int32_t y, int32_t c) {
+    if (!var_ok(h, x) || (y >= 0 && !var_ok(h, y)) || !h) return CSP_EINVAL;
+    h->ne_x.push_back(x);
+    h->ne_y.push_back(y < 0 ? -1 : y);
+    h->ne_c.push_back(c);
+    invalidate(h);
+    return CSP_OK;
+}
+
+int csp_post_int_lin_le(csp_t *h, int32_t k, const int32_t *coef, const int32_t *vars,
+                        int32_t rhs) {
+    if (!h || k < 0 || (k > 0 && (!coef || !vars))) return CSP_EINVAL;
+    std::map<int32_t, int64_t> merged;
+    std::vector<int32_t> order;
+    for (int t = 0; t < k; ++t) {
+        if (!var_ok(h, vars[t])) return CSP_EINVAL;
+        if (!merged.count(vars[t])) order.push_back(vars[t]);
+        merged[vars[t]] += coef[t];
+    }
+    LinRow r;
+    int64_t bound = std::abs((int64_t)rhs);
+    for (int32_t v : order) {
+        const int64_t a = merged[v];
+        if (a == 0) continue;
+        const int64_t mag = std::max(std::abs((int64_t)h->lo[v]), std::abs((int64_t)h->hi[v]));
+        const int64_t win = std::max(std::abs((int64_t)h->lo0), std::abs((int64_t)h->lo0 + 255));
+        bound += std::abs(a) * std::max(mag, win);
+        if (bound >= BOUND_LIMIT) return CSP_ETOOBIG;
+        r.coef.push_back((int32_t)a);
+        r.var.push_back(v);
+    }
+    r.rhs = rhs;
+    h->lin.push_back(r);
+    invalidate(h);
+    return CSP_OK;
+}
+
+int csp_post_alldiff(csp_t *h, int32_t k, const int32_t *vars) {
+    if (!h || k < 0 || (k > 0 && !vars)) return CSP_EINVAL;
+    std::vector<int32_t> g(vars, vars + k);
+    for (int32_t v : g) if (!var_ok(h, v)) return CSP_EINVAL;
+    std::vector<int32_t> s = g;
+    std::sort(s.begin(), s.end());
+    if (std::adjacent_find(s.begin(), s.end()) != s.end()) return CSP_EINVAL;
+    h->ad.push_back(g);
+    invalidate(h);
+    return CSP_OK;
+}
+
+int csp_post_table(csp_t *h, int32_t x, int32_t y, const uint32_t *allowed, int32_t row_words) {
+    if (!var_ok(h, x) || !var_ok(h, y) || x == y || !allowed) return CSP_EINVAL;
+    const int sx = h->hi[x] - h->lo[x] + 1, sy = h->hi[y] - h->lo[y] + 1;
+    if (row_words < (sy + 31) / 32) return CSP_EINVAL;
+    Table T;
+    T.x = x;
+    T.y = y;
+    T.allowed.assign((size_t)sx * sy, 0);
+    for (int a = 0; a < sx; ++a)
+        for (int b = 0; b < sy; ++b)
+            T.allowed[(size_t)a * sy + b] = (allowed[(size_t)a * row_words + b / 32] >> (b % 32)) & 1u;
+    h->tab.push_back(std::move(T));
+    invalidate(h);
+    return CSP_OK;
+}
+
+int csp_layout(const csp_t *h, int32_t *n, int32_t *W, int32_t *lo0) {
+    if (!h) return CSP_EINVAL;
+    if (n) *n = h->n;
+    if (W) *W = h->W;
+    if (lo0) *lo0 = h->lo0;
+    return CSP_OK;
+}
+
+int csp_set_tiling(csp_t *h, const csp_tiling *t) {
+    if (!h) return CSP_EINVAL;
+    h->tiling = t ? *t : csp_tiling{0, 0, 0, 0};
+    if (h->tiling.queue_records & (h->tiling.queue_records - 1)) {
+        h->tiling = csp_tiling{0, 0, 0, 0};
+        return CSP_EINVAL;
+    }
+    invalidate(h);
+    return CSP_OK;
+}
+
+int csp_set_brancher(csp_t *h, int32_t kind, const uint16_t *bf16_weights) {
+    (void)bf16_weights;
+    if (!h) return CSP_EINVAL;
+    if (kind != CSP_BR_FIRST_FAIL) return CSP_EINVAL;
+    h->brancher = kind;
+    return CSP_OK;
+}
+
+int csp_workspace_bytes(const csp_t *hc, int32_t mode, int64_t cap, size_t *bytes) {
+    if (!hc || !bytes || mode < 0 || mode > 2 || cap < 0 || cap > INT32_MAX) return CSP_EINVAL;
+    csp tmp;
+    tmp.n = hc->n; tmp.lo = hc->lo; tmp.hi = hc->hi; tmp.present = hc->present;
+    tmp.ne_x = hc->ne_x; tmp.ne_y = hc->ne_y; tmp.ne_c = hc->ne_c;
+    tmp.lin = hc->lin; tmp.ad = hc->ad; tmp.tab = hc->tab;
+    tmp.lo0 = hc->lo0; tmp.W = hc->W; tmp.tiling = hc->tiling;
+    return plan_single(&tmp, mode, cap, bytes, nullptr);
+}
+
+int csp_bind(csp_t *h, void *dev, size_t bytes, void *cuda_stream) {
+    if (!h || !dev || ((uintptr_t)dev % ALIGN)) return CSP_EINVAL;
+    if (!h->ev0) {
+        if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+            cudaGetLastError();
+            return CSP_ECUDA;
+        }
+    }
+    h->ws = (uint8_t *)dev;
+    h->ws_bytes = bytes;
+    h->stream = (cudaStream_t)cuda_stream;
+    invalidate(h);
+    return CSP_OK;
+}
+
+int csp_upload(csp_t *h, int32_t mode, int64_t cap) {
+    if (!h || mode < 0 || mode > 1 || cap < 0 || cap > INT32_MAX) return CSP_EINVAL;
+    if (!h->ws) return CSP_ESTATE;
+    size_t need = 0;
+    int rc = plan_single(h, mode, cap, &need, &h->block);
+    if (rc) return rc;
+    if (need > h->ws_bytes) return CSP_ENOMEM;
+    const int64_t zero = 0;
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, h->block.data(), h->block.size() * 4,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ws + h->o_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->uploaded = true;
+    h->up_mode = mode;
+    h->up_cap = cap;
+    return CSP_OK;
+}
+
+int csp_launch(csp_t *h, const csp_limits *lim) {
+    if (!h || !h->uploaded) return CSP_ESTATE;
+    SearchArgs A = single_args(h, h->up_mode, h->up_cap, lim);
+    cudaError_t e = cudaMemsetAsync(h->ws + h->o_g, 0, sizeof(GState), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_team, 0, sizeof(Team), h->stream);
+    if (e == cudaSuccess) e = launch_init_single(A, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
+    if (e == cudaSuccess)
+        e = launch_search(h->W, A, h->shape.blocks, h->shape.warps * 32, h->shape.smem, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
+    h->stats.workers = h->shape.blocks * h->shape.warps;
+    h->stats.blocks = h->shape.blocks;
+    return cuda_status(e);
+}
+
+int csp_collect(csp_t *h, int32_t *sol_out) {
+    if (!h || !h->uploaded) return CSP_ESTATE;
+    GState g;
+    cudaError_t e = cudaMemcpyAsync(&g, h->ws + h->o_g, sizeof(g), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int64_t cap = h->up_mode == CSP_FIRST ? 1 : h->up_cap;
+    int64_t stored = std::min<int64_t>((int64_t)g.solutions, cap);
+    if (h->up_mode == CSP_ALL) stored = std::min<int64_t>((int64_t)g.stored, cap);
+    if (sol_out && stored > 0) {
+        e = cudaMemcpyAsync(sol_out, h->ws + h->o_sols, (size_t)stored * h->n * 4,
+                            cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    cudaGetLastError();
+    fill_stats(&h->stats, g, stored);
+    h->stats.ms = ms;
+    h->stats.status = g.status;
+    return g.status;
+}
+
+int csp_solve(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out, const csp_limits *lim) {
+    if (!h) return CSP_EINVAL;
+    if (cap > 0 && !sol_out) return CSP_EINVAL;
+    int rc = csp_upload(h, mode, cap);
+    if (rc) return rc;
+    rc = csp_launch(h, lim);
+    if (rc) return rc;
+    return csp_collect(h, sol_out);
+}
+
+int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom_out,
+                  int32_t *failed) {
+    if (!h || count < 0 || (count > 0 && (!dom_in || !dom_out || !failed))) return CSP_EINVAL;
+    if (!h->ws) return CSP_ESTATE;
+    if (count == 0) return CSP_OK;
+    size_t need = 0;
+    std::vector<uint32_t> B;
+    int rc = plan_single(h, CSP_PROPAGATE, count, &need, &B);
+    if (rc) return rc;
+    if (need > h->ws_bytes) return CSP_ENOMEM;
+    h->uploaded = false;
+    const size_t sw = (size_t)h->n * h->W * 4;
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, B.data(), B.size() * 4,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ws + h->o_qseq, dom_in, sw * count, cudaMemcpyHostToDevice, h->stream);
+    PropArgs P{};
+    P.inst = (const uint32_t *)(h->ws + h->o_inst);
+    P.din = (const uint32_t *)(h->ws + h->o_qseq);
+    P.dout = (uint32_t *)(h->ws + h->o_qrec);
+    P.failed = (int32_t *)(h->ws + h->o_sols);
+    P.count = count;
+    const int cons4 = ((int)B[H_CONS_WORDS] + 3) & ~3;
+    const int warps = 8;
+    const size_t per_warp = (size_t)(((h->n * h->W + 3) & ~3) + 64) * 4;
+    size_t smem = per_warp * warps;
+    P.stage_words = (smem + (size_t)cons4 * 4 <= SMEM_MAX) ? cons4 : 0;
+    smem += (size_t)P.stage_words * 4;
+    if (smem > SMEM_MAX) return CSP_ETOOBIG;
+    const int blocks = std::max(1, std::min(4096, (count + warps - 1) / warps));
+    if (e == cudaSuccess) e = launch_propagate(h->W, P, blocks, warps * 32, smem, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dom_out, h->ws + h->o_qrec, sw * count, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(failed, h->ws + h->o_sols, 4 * (size_t)count, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_status(e);
+}
+
+int csp_stats(const csp_t *h, csp_stats_t *out) {
+    if (!h || !out) return CSP_EINVAL;
+    *out = h->stats;
+    return CSP_OK;
+}
+
+void csp_destroy(csp_t *h) {
+    if (!h) return;
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------- batches
+
+struct csp_batch {
+    std::vector<csp *> hs;
+    int W = 1, R = 4, depth = 2, cons_max = 0;
+    std::vector<uint32_t> arena;
+    std::vector<int64_t> inst_off, sol_off;
+    int64_t sol_words = 0;
+    csp_tiling tiling{0, 0, 0, 0};
+    Shape shape;
+    uint8_t *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool uploaded = false;
+    int32_t mode = -1;
+    size_t o_arena = 0, o_ioff = 0, o_soff = 0, o_g = 0, o_teams = 0, o_qseq = 0, o_qrec = 0,
+           o_spill = 0, o_sols = 0, o_res = 0;
+    cudaGraphExec_t graph = nullptr;
+    int32_t graph_mode = -1;
+    csp_limits graph_lim{};
+    csp_stats_t stats{};
+};
+
+namespace {
+
+int plan_batch(csp_batch *b, int32_t mode, size_t *bytes) {
+    Shape s;
+    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, &s);
+    if (rc) return rc;
+    (void)mode;
+    b->shape = s;
+    const size_t count = b->hs.size();
+    Carver c;
+    b->o_arena = c.take(b->arena.size() * 4);
+    b->o_ioff = c.take(count * 8);
+    b->o_soff = c.take(count * 8);
+    b->o_g = c.take(sizeof(GState));
+    b->o_teams = c.take((size_t)s.blocks * sizeof(Team));
+    b->o_qseq = c.take((size_t)s.blocks * s.qcap * 4);
+    b->o_qrec = c.take((size_t)s.blocks * s.qcap * b->R * 4);
+    b->o_spill = c.take((size_t)s.blocks * s.warps * b->depth * b->R * 4);
+    b->o_sols = c.take((size_t)std::max<int64_t>(b->sol_words, 1) * 4);
+    b->o_res = c.take(count * sizeof(InstResult));
+    *bytes = c.off;
+    return CSP_OK;
+}
+
+SearchArgs batch_args(csp_batch *b, const csp_limits *lim) {
+    SearchArgs A{};
+    uint8_t *w = b->ws;
+    A.arena = (const uint32_t *)(w + b->o_arena);
+    A.inst_off = (const int64_t *)(w + b->o_ioff);
+    A.sol_off = (const int64_t *)(w + b->o_soff);
+    A.n_inst = (int32_t)b->hs.size();
+    A.mode = b->mode;
+    A.batch = 1;
+    A.lsm = b->shape.lsm;
+    A.rmax = b->R;
+    A.depth = b->depth;
+    A.stage_words = b->shape.stage_words;
+    A.qmask = b->shape.qcap - 1;
+    A.flags = lim ? lim->flags : 0;
+    A.warps = b->shape.warps;
+    A.g = (GState *)(w + b->o_g);
+    A.teams = (Team *)(w + b->o_teams);
+    A.qseq = (uint32_t *)(w + b->o_qseq);
+    A.qrec = (uint32_t *)(w + b->o_qrec);
+    A.spill = (uint32_t *)(w + b->o_spill);
+    A.sols = (int32_t *)(w + b->o_sols);
+    A.cap = 0;
+    A.results = (InstResult *)(w + b->o_res);
+    A.node_limit = lim ? lim->node_limit : 0;
+    A.deadline_ns = lim ? lim->time_limit_ns : 0;
+    A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
+    A.mlp = nullptr;
+    return A;
+}
+
+cudaError_t enqueue_batch(csp_batch *b, const SearchArgs &A) {
+    cudaError_t e = cudaMemsetAsync(b->ws + b->o_g, 0, sizeof(GState), b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->ws + b->o_teams, 0, (size_t)b->shape.blocks * sizeof(Team), b->stream);
+    if (e == cudaSuccess) e = launch_init_batch(A, b->shape.blocks, b->stream);
+    if (e == cudaSuccess)
+        e = launch_search(b->W, A, b->shape.blocks, b->shape.warps * 32, b->shape.smem, b->stream);
+    return e;
+}
+
+void drop_graph(csp_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_mode = -1;
+}
+
+bool same_limits(const csp_limits &a, const csp_limits &b) {
+    return a.node_limit == b.node_limit && a.time_limit_ns == b.time_limit_ns &&
+           a.wait_limit_ns == b.wait_limit_ns && a.flags == b.flags;
+}
+
+}  // namespace
+
+extern "C" {
+
+int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count) {
+    if (!out || count < 1 || !hs) return CSP_EINVAL;
+    for (int i = 0; i < count; ++i) if (!hs[i]) return CSP_EINVAL;
+    csp_batch *b = new csp_batch();
+    b->hs.assign(hs, hs + count);
+    int W = 1, nmax = 1;
+    for (csp *h : b->hs) { W = std::max(W, h->W); nmax = std::max(nmax, h->n); }
+    b->W = W;
+    b->depth = nmax + 1;
+    b->R = record_words(nmax * W, W);
+    int64_t sw = 0;
+    for (csp *h : b->hs) {
+        std::vector<uint32_t> B;
+        encode(h, W, B);
+        b->inst_off.push_back((int64_t)b->arena.size());
+        b->arena.insert(b->arena.end(), B.begin(), B.end());
+        b->cons_max = std::max(b->cons_max, (int)B[H_CONS_WORDS]);
+        b->sol_off.push_back(sw);
+        sw += h->n;
+    }
+    b->sol_words = sw;
+    *out = b;
+    return CSP_OK;
+}
+
+int csp_batch_set_tiling(csp_batch_t *b, const csp_tiling *t) {
+    if (!b) return CSP_EINVAL;
+    csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0};
+    if (nt.queue_records & (nt.queue_records - 1)) return CSP_EINVAL;
+    b->tiling = nt;
+    b->uploaded = false;
+    drop_graph(b);
+    return CSP_OK;
+}
+
+int csp_batch_workspace_bytes(const csp_batch_t *bc, int32_t mode, size_t *bytes) {
+    if (!bc || !bytes || mode < 0 || mode > 1) return CSP_EINVAL;
+    csp_batch tmp;
+    tmp.hs = bc->hs; tmp.W = bc->W; tmp.R = bc->R; tmp.depth = bc->depth;
+    tmp.cons_max = bc->cons_max; tmp.arena = bc->arena; tmp.sol_words = bc->sol_words;
+    tmp.tiling = bc->tiling;
+    return plan_batch(&tmp, mode, bytes);
+}
+
+int csp_batch_bind(csp_batch_t *b, void *dev, size_t bytes, void *cuda_stream) {
+    if (!b || !dev || ((uintptr_t)dev % ALIGN)) return CSP_EINVAL;
+    if (!b->ev0) {
+        if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+            cudaGetLastError();
+            return CSP_ECUDA;
+        }
+    }
+    b->ws = (uint8_t *)dev;
+    b->ws_bytes = bytes;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->uploaded = false;
+    drop_graph(b);
+    return CSP_OK;
+}
+
+static int batch_upload(csp_batch *b, int32_t mode) {
+    if (!b->ws) return CSP_ESTATE;
+    size_t need = 0;
+    int rc = plan_batch(b, mode, &need);
+    if (rc) return rc;
+    if (need > b->ws_bytes) return CSP_ENOMEM;
+    const size_t count = b->hs.size();
+    cudaError_t e = cudaMemcpyAsync(b->ws + b->o_arena, b->arena.data(), b->arena.size() * 4,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ws + b->o_ioff, b->inst_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ws + b->o_soff, b->sol_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (b->mode != mode) drop_graph(b);
+    b->mode = mode;
+    b->uploaded = true;
+    return CSP_OK;
+}
+
+int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph) {
+    if (!b || !b->uploaded) return CSP_ESTATE;
+    const csp_limits L = lim ? *lim : csp_limits{0, 0, 0, 0, 0};
+    SearchArgs A = batch_args(b, &L);
+    cudaError_t e = cudaSuccess;
+    if (use_graph) {
+        if (!b->stream) return CSP_EINVAL;      // the legacy stream cannot be captured
+        if (!b->graph || b->graph_mode != b->mode || !same_limits(L, b->graph_lim)) {
+            drop_graph(b);
+            e = set_search_smem(b->W, b->shape.smem);
+            cudaGraph_t g = nullptr;
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = enqueue_batch(b, A);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                e = e1 != cudaSuccess ? e1 : e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) { drop_graph(b); return cuda_status(e); }
+            b->graph_mode = b->mode;
+            b->graph_lim = L;
+        }
+        e = cudaEventRecord(b->ev0, b->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+    } else {
+        e = cudaEventRecord(b->ev0, b->stream);
+        if (e == cudaSuccess) e = enqueue_batch(b, A);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev1, b->stream);
+    b->stats.workers = b->shape.blocks * b->shape.warps;
+    b->stats.blocks = b->shape.blocks;
+    return cuda_status(e);
+}
+
+int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol) {
+    if (!b || !b->uploaded) return CSP_ESTATE;
+    const size_t count = b->hs.size();
+    GState g;
+    std::vector<InstResult> res(count);
+    cudaError_t e = cudaMemcpyAsync(&g, b->ws + b->o_g, sizeof(g), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res.data(), b->ws + b->o_res, count * sizeof(InstResult),
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && sol)
+        e = cudaMemcpyAsync(sol, b->ws + b->o_sols, (size_t)b->sol_words * 4, cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (out)
+        for (size_t i = 0; i < count; ++i) {
+            out[i].status = res[i].status;
+            out[i].n = b->hs[i]->n;
+            out[i].nodes = res[i].nodes;
+            out[i].fails = res[i].fails;
+            out[i].solutions = res[i].solutions;
+            out[i].sol_offset = b->sol_off[i];
+        }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    cudaGetLastError();
+    fill_stats(&b->stats, g, 0);
+    b->stats.ms = ms;
+    b->stats.status = g.status;
+    return g.status;
+}
+
+int csp_batch_solve(csp_batch_t *b, int32_t mode, const csp_limits *lim, int32_t use_graph,
+                    csp_result *out, int32_t *sol) {
+    if (!b || mode < 0 || mode > 1) return CSP_EINVAL;
+    if (!b->uploaded || b->mode != mode) {
+        int rc = batch_upload(b, mode);
+        if (rc) return rc;
+    }
+    int rc = csp_batch_launch(b, lim, use_graph);
+    if (rc) return rc;
+    return csp_batch_collect(b, out, sol);
+}
+
+int64_t csp_batch_solution_words(const csp_batch_t *b) { return b ? b->sol_words : 0; }
+
+int csp_batch_stats(const csp_batch_t *b, csp_stats_t *out) {
+    if (!b || !out) return CSP_EINVAL;
+    *out = b->stats;
+    return CSP_OK;
+}
+
+void csp_batch_destroy(csp_batch_t *b) {
+    if (!b) return;
+    drop_graph(b);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    cudaGetLastError();
+    delete b;
+}
+
+const char *csp_strerror(int code) {
+    switch (code) {
+    case CSP_OK: return "ok";
+    case CSP_EINVAL: return "invalid argument";
+    case CSP_ENOMEM: return "workspace too small";
+    case CSP_ETOOBIG: return "problem exceeds supported sizes";
+    case CSP_ECUDA: return "CUDA error or no device";
+    case CSP_ELIMIT: return "node or time limit reached";
+    case CSP_ETIMEOUT: return "device-side wait limit exceeded";
+    case CSP_ESTATE: return "call out of order";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal layout shared by the library's host encoder and its CUDA kernels.
+//
+// One problem is encoded as a flat array of uint32 words ("instance block").  The first
+// HDR_WORDS words are a header of offsets (in words, from the start of the block); then the
+// constraint data, which blocks stage into shared memory; then the root domains.
+//
+// Domains are bitsets of W words: bit k of variable i's domain (word i*W + k/32) stands for
+// the value lo0 + k.  All variables of an instance share lo0 and W.
+#pragma once
+#include <stdint.h>
+
+namespace cubics {
+
+constexpr int MAX_VARS = 1024;          // NW = ceil(n/32) <= 32 event words per worker
+constexpr int MAX_W = 8;                // 256-value window
+constexpr int HDR_WORDS = 32;
+constexpr uint32_t FLAG_TRIVIAL_FAIL = 1u;  // a row with no terms and rhs < 0
+constexpr int WS_WORDS = 88;            // per-warp shared bookkeeping (events, counters)
+
+enum Hdr {
+    H_N = 0, H_W, H_LO0, H_S, H_NW, H_FLAGS,
+    H_N_UN, H_OFF_UN,                 // unary x != c: (x | bit << 16)
+    H_OFF_ADJ_START, H_OFF_ADJ,       // ne adjacency: n+1 starts; (other | (uint16)off << 16)
+    H_N_LIN, H_OFF_LIN_ROW, H_OFF_LIN_TERM, H_LIN_MW, H_OFF_LIN_MASK,
+    H_N_AD, H_OFF_AD_ROW, H_OFF_AD_MEM, H_AD_MW, H_OFF_AD_MASK,
+    H_N_TAB, H_OFF_TAB,
+    H_OFF_ROOT, H_CONS_WORDS, H_TOTAL, H_R, H_N_NE,
+    H_COUNT
+};
+static_assert(H_COUNT <= HDR_WORDS, "header too long");
+
+// lin row: 3 words (first term, number of terms, rhs); term: 2 words (coef, var)
+// alldiff group: 2 words (first member, number of members)
+// table: 4 words (x, y, word offset of R, word offset of C); R and C hold 32*W rows of W
+//        words: R row a = values of y compatible with x = lo0 + a, C row b the transpose.
+
+// Search-stack level / work record: R words = S domain words, W words of values still to
+// try, one word with the branching variable (-1: the record is a node to propagate).
+__host__ __device__ inline int record_words(int S, int W) { return (S + W + 1 + 3) & ~3; }
+
+struct Team {                 // one work-sharing group (whole grid or one block)
+    int32_t work;             // records queued or being explored
+    int32_t idle;             // workers waiting for a record
+    uint32_t head, tail;      // queue positions
+    int32_t found;            // CSP_FIRST: a solution was recorded
+    int32_t inst;             // instance index (batch mode)
+    int32_t pad[26];          // one 128-byte line per team
+};
+
+struct GState {               // counters of one launch
+    unsigned long long nodes, fails, solutions, hsum, hxor, evals, steals, spills;
+    unsigned long long stored;        // solution slots taken
+    unsigned long long node_progress; // for the node limit
+    int32_t max_depth;
+    int32_t status;                   // 0 ok, else CSP_E*
+    int32_t abort;                    // global stop
+    int32_t ticket;                   // next batch instance
+    int32_t pad[24];
+};
+
+struct InstResult {
+    int32_t status;           // 1 SAT, 0 UNSAT, < 0 error
+    int32_t n;
+    unsigned long long nodes, fails, solutions;
+    int64_t sol_offset;
+};
+
+struct SearchArgs {
+    const uint32_t *arena;    // instance blocks
+    const int64_t *inst_off;  // word offset of each instance block
+    const int64_t *sol_off;   // batch: offset of each instance's solution slot in `sols`
+    int32_t n_inst;
+    int32_t mode;             // 0 all, 1 first
+    int32_t batch;            // 0: one team = grid; 1: one team per block, instance tickets
+    int32_t lsm;              // stack levels in shared memory per worker
+    int32_t rmax;             // record words (max over instances)
+    int32_t depth;            // stack levels per worker (max n + 1)
+    int32_t stage_words;      // shared-memory words reserved for constraint data
+    int32_t qmask;            // queue capacity - 1
+    int32_t flags;
+    int32_t warps;            // workers per block
+    GState *g;
+    Team *teams;
+    uint32_t *qseq;           // per team: qcap sequence words
+    uint32_t *qrec;           // per team: qcap records of rmax words
+    uint32_t *spill;          // per worker: depth records of rmax words
+    int32_t *sols;
+    int64_t cap;
+    InstResult *results;
+    long long node_limit;
+    long long deadline_ns;    // time limit from each worker's start, 0 = none
+    long long wait_limit_ns;
+    const uint16_t *mlp;      // learned brancher weights (bf16), NULL = first-fail
+};
+
+struct PropArgs {
+    const uint32_t *inst;
+    const uint32_t *din;
+    uint32_t *dout;
+    int32_t *failed;
+    int32_t count;
+    int32_t stage_words;
+};
+
+}  // namespace cubics

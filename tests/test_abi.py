@@ -1,0 +1,91 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry point, and its
+host-side validation answers with the documented status codes (no device calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1909_09213_gb300 import cubics as K
+from paper_1909_09213_gb300 import instances as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            text = open(os.path.join(inc, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(csp_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = K.lib()
+    names = declared_functions()
+    assert len(names) >= 29
+    for n in names:
+        assert hasattr(L, n), n
+    assert names == set(K.SIGNATURES), "binding and header must list the same entry points"
+
+
+def _create(n, lo, hi):
+    h = C.c_void_p()
+    lo = np.asarray(lo, np.int32)
+    hi = np.asarray(hi, np.int32)
+    rc = K.lib().csp_create(C.byref(h), n, lo.ctypes.data_as(K._I32P), hi.ctypes.data_as(K._I32P))
+    return rc, h
+
+
+def test_create_validation():
+    assert _create(0, [], [])[0] == K.CSP_EINVAL
+    assert _create(1, [3], [2])[0] == K.CSP_EINVAL
+    assert _create(1025, [0] * 1025, [1] * 1025)[0] == K.CSP_ETOOBIG
+    assert _create(2, [0, 200], [10, 300])[0] == K.CSP_ETOOBIG      # window of 301 values
+    rc, h = _create(2, [-5, 0], [5, 250])
+    assert rc == K.CSP_OK
+    n, W, lo0 = C.c_int32(), C.c_int32(), C.c_int32()
+    assert K.lib().csp_layout(h, C.byref(n), C.byref(W), C.byref(lo0)) == 0
+    assert (n.value, W.value, lo0.value) == (2, 8, -5)
+    K.lib().csp_destroy(h)
+
+
+def test_post_validation():
+    L = K.lib()
+    rc, h = _create(3, [0, 0, 0], [9, 9, 9])
+    assert rc == 0
+    assert L.csp_post_int_ne(h, 0, 3, 1) == K.CSP_EINVAL
+    assert L.csp_post_int_ne(h, 0, -1, 4) == K.CSP_OK
+    v = np.array([0, 0], np.int32)
+    assert L.csp_post_alldiff(h, 2, v.ctypes.data_as(K._I32P)) == K.CSP_EINVAL
+    a = np.array([1 << 29, 1 << 29], np.int32)
+    v = np.array([0, 1], np.int32)
+    assert L.csp_post_int_lin_le(h, 2, a.ctypes.data_as(K._I32P), v.ctypes.data_as(K._I32P), 0) == K.CSP_ETOOBIG
+    t = np.ones(10, np.uint32)
+    assert L.csp_post_table(h, 1, 1, t.ctypes.data_as(K._U32P), 1) == K.CSP_EINVAL
+    assert L.csp_post_table(h, 1, 2, t.ctypes.data_as(K._U32P), 0) == K.CSP_EINVAL
+    assert L.csp_post_table(h, 1, 2, t.ctypes.data_as(K._U32P), 1) == K.CSP_OK
+    assert L.csp_set_tiling(h, C.byref(K.tiling(queue_records=100))) == K.CSP_EINVAL
+    assert L.csp_launch(h, None) == K.CSP_ESTATE          # nothing uploaded
+    L.csp_destroy(h)
+
+
+def test_workspace_size_grows_with_cap():
+    p = K.Csp(I.queens(6))
+    p.set_tiling(K.tiling(blocks=2, warps_per_block=4))
+    b0 = p.workspace_bytes(K.CSP_ALL, 0)
+    b1 = p.workspace_bytes(K.CSP_ALL, 1000)
+    assert b1 >= b0 + 999 * 6 * 4 - 256
+    assert p.workspace_bytes(K.CSP_PROPAGATE, 10) > 0
+
+
+def test_models_build_through_the_abi():
+    for m in [I.queens(8), I.worked_example("lin", "table"), I.model_rb(1, 20, 8),
+              I.lin_alldiff(3), I.random_tiny(5)]:
+        p = K.Csp(m)
+        n, W, lo0 = p.layout()
+        assert n == m.n and W in (1, 2, 4, 8) and lo0 == min(m.lo)

@@ -1,0 +1,311 @@
+"""GPU parity: the CUDA path against the oracle on the same seeded inputs.
+
+Propagation must be bit-exact (same fixpoint domains, same failure flag); search must give
+the same solution count, solution-set hash, sorted solution list, node count and fail count
+as the oracle's sequential search (the tree is fixed by the per-node fixpoints and the
+first-fail rule, so it does not depend on how workers share it).
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1909_09213_gb300 import cubics as K
+from paper_1909_09213_gb300 import instances as I
+
+from _util import bits_to_flags, flags_to_bits, random_subdomains, sorted_rows
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def queens_count(N):
+    for ln in open(os.path.join(GOLDEN, "queens_counts.txt")):
+        if ln.strip() and not ln.startswith("#"):
+            a, b = map(int, ln.split())
+            if a == N:
+                return b
+    raise KeyError(N)
+
+
+def mixed_model(seed, span=40, n=7):
+    """Every constraint kind over a window wider than one word (W = 2 or more)."""
+    s = I.Stream(seed)
+    lo = [int(v) for v in s.ints(-3, 3, n)]
+    hi = [lo[i] + int(s.int(span // 2, span - 7)) for i in range(n)]
+    m = I.CspModel(n=n, lo=lo, hi=hi, name=f"mixed-{span}-{seed}")
+    for i in range(n):
+        for _ in range(3):
+            m.removed.append((i, s.int(lo[i], hi[i])))
+    m.ne.append((0, 1, 3))
+    m.ne.append((2, -1, lo[2] + 1))
+    m.ne.append((3, 4, -7))
+    last = n - 1
+    m.lin.append(([2, -3, 1], [0, 1, 2], 5))
+    m.lin.append(([-1, -1, 1, 4], [3, 4, last, last], -2))    # repeated variable: merged
+    m.alldiff.append([1, 3, 5, 6] if n >= 7 else [1, n - 2, last])
+    sx, sy = hi[2] - lo[2] + 1, hi[last] - lo[last] + 1
+    al = (s.ints(0, 2, sx * sy) > 0).reshape(sx, sy)
+    m.tables.append((2, last, al))
+    return m
+
+
+# ----------------------------------------------------------------------------- propagation
+
+def propagate_parity(m, rng, count):
+    om = O.OracleModel(m)
+    p = K.Csp(m)
+    n, W, lo0 = p.layout()
+    subs = random_subdomains(om, rng, count)
+    din = np.stack([flags_to_bits(om, f, n, W, lo0) for f in subs])
+    dout, failed = p.propagate(din)
+    n_fail = 0
+    for k, f in enumerate(subs):
+        of, od = O.propagate(om, f, variant=1)
+        assert bool(failed[k]) == of, (m.name, k)
+        if of:
+            n_fail += 1
+            continue
+        got = bits_to_flags(om, dout[k], n, W, lo0)
+        assert np.array_equal(got, od), (m.name, k, om.flags_to_sets(od), om.flags_to_sets(got))
+    ok = ~failed
+    if ok.any():                                         # idempotence on the device
+        d2, f2 = p.propagate(dout[ok])
+        assert not f2.any() and np.array_equal(d2, dout[ok])
+    return n_fail
+
+
+def test_propagate_tiny_random():
+    rng = np.random.default_rng(1)
+    fails = 0
+    for i in range(250):
+        m = I.random_tiny(I.seed_for(I.CFG_TINY, 50000 + i))
+        fails += propagate_parity(m, rng, 6)
+    assert fails > 50
+
+
+@pytest.mark.parametrize("span", [40, 100, 250])
+def test_propagate_multiword(span):
+    rng = np.random.default_rng(span)
+    for seed in range(6):
+        propagate_parity(mixed_model(seed, span), rng, 20)
+
+
+def test_propagate_queens_rb_linad():
+    rng = np.random.default_rng(2)
+    propagate_parity(I.queens(8), rng, 64)
+    propagate_parity(I.queens(16), rng, 64)
+    propagate_parity(I.model_rb(11, 20, 8), rng, 32)
+    propagate_parity(I.model_rb(12, 30, 32), rng, 32)
+    propagate_parity(I.lin_alldiff(13, n=40, rows=12, groups=4), rng, 16)
+
+
+def test_propagate_root_linad_full_size():
+    rng = np.random.default_rng(3)
+    propagate_parity(I.lin_alldiff(I.seed_for(I.CFG_LINAD, 0)), rng, 4)
+
+
+def test_propagate_empty_and_singletons():
+    m = I.queens(6)
+    om = O.OracleModel(m)
+    p = K.Csp(m)
+    n, W, lo0 = p.layout()
+    empty = np.zeros(n * W, np.uint32)
+    single = np.zeros(n * W, np.uint32)
+    for i in range(n):                                     # a full solution: 1 3 5 0 2 4
+        single[i] = 1 << [1, 3, 5, 0, 2, 4][i]
+    dout, failed = p.propagate(np.stack([empty, single]))
+    assert failed[0] and not failed[1] and np.array_equal(dout[1], single)
+
+
+# ----------------------------------------------------------------------------- search
+
+TILINGS = {
+    "auto": None,
+    "one-worker": K.tiling(blocks=1, warps_per_block=1),
+    "spilling": K.tiling(blocks=3, warps_per_block=4, smem_levels=2, queue_records=8),
+}
+
+
+def search_parity(m, tiling=None, cap=5000):
+    om = O.OracleModel(m)
+    r = O.solve(om, cap=cap, variant=1)
+    p = K.Csp(m)
+    if tiling is not None:
+        p.set_tiling(tiling)
+    rc, st, sols = p.solve(K.CSP_ALL, cap)
+    assert rc == 0, m.name
+    assert st["solutions"] == r.solutions, m.name
+    assert (st["sol_hash_sum"], st["sol_hash_xor"]) == (r.hash_sum, r.hash_xor), m.name
+    assert (st["nodes"], st["fails"]) == (r.nodes, r.fails), m.name
+    if r.solutions <= cap:
+        assert sorted_rows(sols) == sorted_rows(r.sols), m.name
+    return st
+
+
+@pytest.mark.parametrize("tname", list(TILINGS))
+def test_search_queens_small(tname):
+    for N in range(1, 11):
+        st = search_parity(I.queens(N), TILINGS[tname])
+        assert st["solutions"] == queens_count(N)
+
+
+@pytest.mark.parametrize("c1", ["domain", "lin"])
+@pytest.mark.parametrize("c2", ["lin", "table"])
+def test_search_worked_example(c1, c2):
+    st = search_parity(I.worked_example(c1, c2))
+    assert st["solutions"] == 11
+
+
+@pytest.mark.parametrize("tname", list(TILINGS))
+def test_search_tiny_random(tname):
+    for i in range(120):
+        search_parity(I.random_tiny(I.seed_for(I.CFG_TINY, 70000 + i)), TILINGS[tname])
+
+
+def test_search_multiword_and_rb():
+    for seed in range(4):
+        search_parity(mixed_model(100 + seed, 40, 5), cap=100000)
+    for k in range(6):
+        search_parity(I.model_rb(I.seed_for(I.CFG_RB, 900 + k), 12, 6), cap=100000)
+
+
+def test_search_spill_heavy_deep_stack():
+    # 12-queens with 2 shared-memory levels per worker: most levels live in global memory
+    st = search_parity(I.queens(12), K.tiling(blocks=4, warps_per_block=8, smem_levels=2), cap=10)
+    assert st["spills"] > 0
+
+
+def test_first_mode_status_and_validity():
+    for i in range(150):
+        m = I.random_tiny(I.seed_for(I.CFG_TINY, 80000 + i))
+        om = O.OracleModel(m)
+        r = O.solve(om, mode=1, cap=1)
+        p = K.Csp(m)
+        rc, st, sols = p.solve(K.CSP_FIRST)
+        assert rc == 0
+        assert st["solutions"] == (1 if r.status == 1 else 0), m.name
+        if r.status == 1:
+            assert O.check_solution(om, sols[0]), m.name
+
+
+def test_first_mode_single_worker_is_the_oracle_order():
+    for m in [I.queens(8), I.queens(12), I.model_rb(I.seed_for(I.CFG_RB, 7), 25, 10)]:
+        om = O.OracleModel(m)
+        r = O.solve(om, mode=1, cap=1)
+        p = K.Csp(m)
+        p.set_tiling(K.tiling(blocks=1, warps_per_block=1))
+        rc, st, sols = p.solve(K.CSP_FIRST)
+        assert rc == 0 and st["solutions"] == r.solutions
+        assert (st["nodes"], st["fails"]) == (r.nodes, r.fails)
+        if r.solutions:
+            assert tuple(sols[0]) == tuple(r.sols[0])
+
+
+def test_queens_14_full_size():
+    p = K.Csp(I.queens(14))
+    rc, st, _ = p.solve(K.CSP_ALL, 0)
+    assert rc == 0 and st["solutions"] == queens_count(14)
+
+
+def test_queens_16_full_size_and_sampled_subtrees():
+    """16-queens in the benchmark's launch shape: the published count; nodes, fails and the
+    solution hash of sampled subtrees (x0, x1 fixed) against the oracle."""
+    p = K.Csp(I.queens(16))
+    rc, st, _ = p.solve(K.CSP_ALL, 0)
+    assert rc == 0 and st["solutions"] == queens_count(16)
+    assert st["steals"] > 0
+    for (a, b) in [(0, 2), (7, 3)]:
+        m = I.queens(16)
+        m.removed += [(0, v) for v in range(16) if v != a] + [(1, v) for v in range(16) if v != b]
+        search_parity(m, cap=0)
+
+
+# ----------------------------------------------------------------------------- limits, errors
+
+def test_node_limit():
+    p = K.Csp(I.queens(11))
+    p.set_tiling(K.tiling(blocks=1, warps_per_block=2))      # limits are checked every 64 nodes
+    rc, st, _ = p.solve(K.CSP_ALL, 0, K.limits(node_limit=200))
+    assert rc == K.CSP_ELIMIT and st["nodes"] >= 200
+
+
+def test_wait_limit_returns_timeout():
+    # no worker ever donates, so every idle worker waits until the limit runs out
+    p = K.Csp(I.queens(13))
+    rc, st, _ = p.solve(K.CSP_ALL, 0, K.limits(wait_limit_ns=20_000_000, flags=K.CSP_F_NO_DONATE))
+    assert rc == K.CSP_ETIMEOUT
+    rc, st, _ = p.solve(K.CSP_ALL, 0)                       # the context is still usable
+    assert rc == 0 and st["solutions"] == queens_count(13)
+
+
+def test_small_workspace_is_enomem():
+    import ctypes as C
+    p = K.Csp(I.queens(8))
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    L = K.lib()
+    assert L.csp_bind(p.h, C.c_void_p(ws.data_ptr()), 1024, None) == 0
+    sols = np.zeros((1, 8), np.int32)
+    assert L.csp_solve(p.h, K.CSP_ALL, 0, sols.ctypes.data_as(K._I32P), None) == K.CSP_ENOMEM
+
+
+# ----------------------------------------------------------------------------- batches
+
+def _rb_small(count, first=0):
+    return I.rb_batch(count, n_range=(8, 16), d_range=(4, 9), config_id=I.CFG_RB + 100, first=first)
+
+
+def test_batch_first_matches_oracle_status():
+    models = _rb_small(96)
+    probs = [K.Csp(m) for m in models]
+    b = K.Batch(probs)
+    rc, res = b.solve(K.CSP_FIRST)
+    assert rc == 0
+    sat = 0
+    for m, r in zip(models, res):
+        om = O.OracleModel(m)
+        o = O.solve(om, mode=1, cap=1)
+        assert r["status"] == o.status, m.name
+        if o.status == 1:
+            sat += 1
+            assert O.check_solution(om, r["solution"]), m.name
+    assert 0 < sat < len(models)
+
+
+def test_batch_all_counts_and_graph_replay():
+    models = _rb_small(48, first=500)
+    b = K.Batch([K.Csp(m) for m in models])
+    rc, res = b.solve(K.CSP_ALL)
+    assert rc == 0
+    for m, r in zip(models, res):
+        o = O.solve(O.OracleModel(m), variant=1)
+        assert (r["solutions"], r["nodes"], r["fails"]) == (o.solutions, o.nodes, o.fails), m.name
+    rc, res_g = b.solve(K.CSP_ALL, use_graph=True)
+    rc2, res_g2 = b.solve(K.CSP_ALL, use_graph=True)
+    assert rc == 0 and rc2 == 0
+    strip = lambda rs: [(r["status"], r["solutions"], r["nodes"]) for r in rs]
+    assert strip(res_g) == strip(res) == strip(res_g2)
+
+
+def test_batch_tilings_do_not_change_results():
+    models = _rb_small(40, first=900)
+    probs = [K.Csp(m) for m in models]
+    out = []
+    for t in [K.tiling(warps_per_block=1), K.tiling(warps_per_block=8, smem_levels=2),
+              K.tiling(blocks=5, warps_per_block=4)]:
+        b = K.Batch(probs)
+        b.set_tiling(t)
+        rc, res = b.solve(K.CSP_ALL)
+        assert rc == 0
+        out.append([(r["solutions"], r["nodes"], r["fails"]) for r in res])
+    assert out[0] == out[1] == out[2]
