@@ -82,6 +82,8 @@ typedef struct {
     int64_t stored;          /* solutions written to sol_out */
     int32_t workers;         /* workers (warps) of the last launch */
     int32_t blocks;          /* blocks of the last launch */
+    int64_t h2d_bytes;       /* host-to-device bytes of the last upload */
+    int64_t d2h_bytes;       /* device-to-host bytes of the last collect */
 } csp_stats_t;
 
 typedef struct {
@@ -190,6 +192,15 @@ int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol);
 int64_t csp_batch_solution_words(const csp_batch_t *b);
 int csp_batch_stats(const csp_batch_t *b, csp_stats_t *out);
 void csp_batch_destroy(csp_batch_t *b);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Shared-memory bandwidth of the current device (a measurement helper with no counterpart
+ * in the paper; it is the denominator of the search kernel's roofline).  Every SM streams
+ * 128-bit ld.shared over a 64 KB buffer; *gbs receives bytes read / kernel time in GB/s
+ * (best of `reps` launches).  dev_out: device buffer of at least 16 bytes that receives a
+ * checksum so the loads are not optimised away.  Synchronises `cuda_stream`. */
+int csp_probe_smem_bandwidth(void *dev_out, void *cuda_stream, int32_t reps, double *gbs);
 
 #ifdef __cplusplus
 }

@@ -14,14 +14,14 @@
 #include "internal.h"
 
 namespace cubics {
-cudaError_t launch_search(int W, const SearchArgs &A, int blocks, int threads, size_t smem,
-                          cudaStream_t st);
-cudaError_t occupancy_search(int W, int threads, size_t smem, int *blocks_per_sm);
-cudaError_t set_search_smem(int W, size_t smem);
+cudaError_t launch_search(int W, bool staged, const SearchArgs &A, int blocks, int threads,
+                          size_t smem, cudaStream_t st);
+cudaError_t occupancy_search(int W, bool staged, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_init_single(const SearchArgs &A, cudaStream_t st);
 cudaError_t launch_init_batch(const SearchArgs &A, int teams, cudaStream_t st);
-cudaError_t launch_propagate(int W, const PropArgs &P, int blocks, int threads, size_t smem,
-                             cudaStream_t st);
+cudaError_t launch_propagate(int W, bool staged, const PropArgs &P, int blocks, int threads,
+                             size_t smem, cudaStream_t st);
+cudaError_t probe_smem(void *out, cudaStream_t st, int sms, int reps, double *gbs);
 }  // namespace cubics
 
 using namespace cubics;
@@ -90,7 +90,8 @@ int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batc
         DeviceInfo di = device_info();
         if (!di.ok) return CSP_ECUDA;
         int bps = 0;
-        if (occupancy_search(W, s->warps * 32, s->smem, &bps) != cudaSuccess || bps < 1) {
+        if (occupancy_search(W, s->stage_words > 0, s->warps * 32, s->smem, &bps) != cudaSuccess ||
+            bps < 1) {
             cudaGetLastError();
             return CSP_ECUDA;
         }
@@ -134,6 +135,9 @@ struct csp {
     int32_t up_mode = -1;
     int64_t up_cap = 0;
     std::vector<uint32_t> block;
+    uint32_t *pin_block = nullptr;   // pinned host staging of the encoded problem
+    size_t pin_words = 0;
+    GState *pin_g = nullptr;         // pinned host copy of the launch counters
     Shape shape;
     size_t o_inst = 0, o_off = 0, o_g = 0, o_team = 0, o_qseq = 0, o_qrec = 0, o_spill = 0,
            o_sols = 0;
@@ -507,13 +511,34 @@ int csp_upload(csp_t *h, int32_t mode, int64_t cap) {
     int rc = plan_single(h, mode, cap, &need, &h->block);
     if (rc) return rc;
     if (need > h->ws_bytes) return CSP_ENOMEM;
-    const int64_t zero = 0;
-    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, h->block.data(), h->block.size() * 4,
+    // stage through pinned host memory: the encoded problem, then its block offset (0)
+    const size_t words = h->block.size() + 2;
+    if (h->pin_words < words) {
+        if (h->pin_block) cudaFreeHost(h->pin_block);
+        h->pin_block = nullptr;
+        h->pin_words = 0;
+        if (cudaMallocHost(&h->pin_block, words * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return CSP_ECUDA;
+        }
+        h->pin_words = words;
+    }
+    if (!h->pin_g && cudaMallocHost(&h->pin_g, sizeof(GState)) != cudaSuccess) {
+        cudaGetLastError();
+        h->pin_g = nullptr;
+        return CSP_ECUDA;
+    }
+    std::memcpy(h->pin_block, h->block.data(), h->block.size() * 4);
+    h->pin_block[h->block.size()] = 0u;
+    h->pin_block[h->block.size() + 1] = 0u;
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, h->pin_block, h->block.size() * 4,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->ws + h->o_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(h->ws + h->o_off, h->pin_block + h->block.size(), sizeof(int64_t),
+                            cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    h->stats.h2d_bytes = (int64_t)h->block.size() * 4 + (int64_t)sizeof(int64_t);
     h->uploaded = true;
     h->up_mode = mode;
     h->up_cap = cap;
@@ -528,7 +553,8 @@ int csp_launch(csp_t *h, const csp_limits *lim) {
     if (e == cudaSuccess) e = launch_init_single(A, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess)
-        e = launch_search(h->W, A, h->shape.blocks, h->shape.warps * 32, h->shape.smem, h->stream);
+        e = launch_search(h->W, h->shape.stage_words > 0, A, h->shape.blocks, h->shape.warps * 32,
+                          h->shape.smem, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
     h->stats.workers = h->shape.blocks * h->shape.warps;
     h->stats.blocks = h->shape.blocks;
@@ -536,11 +562,13 @@ int csp_launch(csp_t *h, const csp_limits *lim) {
 }
 
 int csp_collect(csp_t *h, int32_t *sol_out) {
-    if (!h || !h->uploaded) return CSP_ESTATE;
-    GState g;
-    cudaError_t e = cudaMemcpyAsync(&g, h->ws + h->o_g, sizeof(g), cudaMemcpyDeviceToHost, h->stream);
+    if (!h || !h->uploaded || !h->pin_g) return CSP_ESTATE;
+    cudaError_t e = cudaMemcpyAsync(h->pin_g, h->ws + h->o_g, sizeof(GState),
+                                    cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    const GState g = *h->pin_g;
+    int64_t d2h = sizeof(GState);
     const int64_t cap = h->up_mode == CSP_FIRST ? 1 : h->up_cap;
     int64_t stored = std::min<int64_t>((int64_t)g.solutions, cap);
     if (h->up_mode == CSP_ALL) stored = std::min<int64_t>((int64_t)g.stored, cap);
@@ -549,6 +577,7 @@ int csp_collect(csp_t *h, int32_t *sol_out) {
                             cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_status(e);
+        d2h += stored * h->n * 4;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -556,6 +585,7 @@ int csp_collect(csp_t *h, int32_t *sol_out) {
     fill_stats(&h->stats, g, stored);
     h->stats.ms = ms;
     h->stats.status = g.status;
+    h->stats.d2h_bytes = d2h;
     return g.status;
 }
 
@@ -599,7 +629,8 @@ int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom
     smem += (size_t)P.stage_words * 4;
     if (smem > SMEM_MAX) return CSP_ETOOBIG;
     const int blocks = std::max(1, std::min(4096, (count + warps - 1) / warps));
-    if (e == cudaSuccess) e = launch_propagate(h->W, P, blocks, warps * 32, smem, h->stream);
+    if (e == cudaSuccess)
+        e = launch_propagate(h->W, P.stage_words > 0, P, blocks, warps * 32, smem, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dom_out, h->ws + h->o_qrec, sw * count, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess)
@@ -618,6 +649,8 @@ void csp_destroy(csp_t *h) {
     if (!h) return;
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->pin_block) cudaFreeHost(h->pin_block);
+    if (h->pin_g) cudaFreeHost(h->pin_g);
     cudaGetLastError();
     delete h;
 }
@@ -709,7 +742,8 @@ cudaError_t enqueue_batch(csp_batch *b, const SearchArgs &A) {
         e = cudaMemsetAsync(b->ws + b->o_teams, 0, (size_t)b->shape.blocks * sizeof(Team), b->stream);
     if (e == cudaSuccess) e = launch_init_batch(A, b->shape.blocks, b->stream);
     if (e == cudaSuccess)
-        e = launch_search(b->W, A, b->shape.blocks, b->shape.warps * 32, b->shape.smem, b->stream);
+        e = launch_search(b->W, b->shape.stage_words > 0, A, b->shape.blocks, b->shape.warps * 32,
+                          b->shape.smem, b->stream);
     return e;
 }
 
@@ -818,7 +852,9 @@ int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph) {
         if (!b->stream) return CSP_EINVAL;      // the legacy stream cannot be captured
         if (!b->graph || b->graph_mode != b->mode || !same_limits(L, b->graph_lim)) {
             drop_graph(b);
-            e = set_search_smem(b->W, b->shape.smem);
+            int bps = 0;   // sets the kernel's shared-memory attribute outside the capture
+            e = occupancy_search(b->W, b->shape.stage_words > 0, b->shape.warps * 32, b->shape.smem,
+                                 &bps);
             cudaGraph_t g = nullptr;
             if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
@@ -903,6 +939,13 @@ void csp_batch_destroy(csp_batch_t *b) {
     if (b->ev1) cudaEventDestroy(b->ev1);
     cudaGetLastError();
     delete b;
+}
+
+int csp_probe_smem_bandwidth(void *dev_out, void *cuda_stream, int32_t reps, double *gbs) {
+    if (!dev_out || !gbs || reps < 1) return CSP_EINVAL;
+    DeviceInfo di = device_info();
+    if (!di.ok) return CSP_ECUDA;
+    return cuda_status(probe_smem(dev_out, (cudaStream_t)cuda_stream, di.sms, reps, gbs));
 }
 
 const char *csp_strerror(int code) {

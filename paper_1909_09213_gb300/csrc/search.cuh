@@ -1,0 +1,578 @@
+// CUBICS search kernels for sm_103a (arxiv 1909.09213, Sections 2.1-2.3).
+//
+// The whole search stays on the GPU (Section 2.1).  One warp is one worker: it owns a
+// depth-first stack of search levels, labels one variable per level (d-way, values
+// ascending), propagates each child to its fixpoint and backtracks on failure.  Each level
+// is a full copy of the parent's domains plus the values still to try, so backtracking is
+// a restore of one record: the copy is parallel over the domain words (the per-domain
+// save/restore of Section 2.2), done by the 32 lanes.  The top levels of each stack live
+// in shared memory (Section 2.3); deeper ones spill to a private global-memory area.
+//
+// Idle workers take records (a parent state with untried values) from a work queue; busy
+// workers donate their shallowest untried values when someone is idle (search-space
+// partitioning with a task pool, Section 1.3).  In single-problem mode the team is the whole
+// grid; in batch mode each block is a team that solves one instance after another.
+//
+// Included by one translation unit per domain width W (kernels_w*.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "device.cuh"
+
+namespace cubics {
+
+constexpr int CSP_ELIMIT_ = -5;
+constexpr int CSP_ETIMEOUT_ = -6;
+constexpr int F_NO_DONATE = 1;
+
+// launch arguments, copied once per block into shared memory
+static __shared__ SearchArgs SA;
+
+// per-warp bookkeeping kept in shared memory (lane 0 writes the counters)
+struct WarpShared {
+    uint32_t chg[32], evs[32];
+    unsigned long long nodes, fails, sols, hsum, hxor, evals, steals, spills;
+    long long t_start;
+    int64_t sol_off;
+    int32_t maxd, pad[3];
+};
+static_assert(sizeof(WarpShared) == 4 * WS_WORDS, "WarpShared size must match WS_WORDS");
+
+// ------------------------------------------------------------------ work queue
+// Bounded multi-producer multi-consumer ring (per-slot sequence numbers).  Lane 0 claims a
+// position; the warp copies the record; a release store of the sequence publishes it.
+
+// Claims a slot; returns its position, or -1 when full/empty after bounded retries.
+__device__ __forceinline__ long long q_claim(uint32_t *ctr, const uint32_t *seq, uint32_t qmask,
+                                             bool push) {
+    uint32_t pos = ld_volatile(ctr);
+    for (int it = 0; it < 256; ++it) {
+        const uint32_t s = ld_acquire(&seq[pos & qmask]);
+        const int dif = (int)(s - (push ? pos : pos + 1));
+        if (dif == 0) {
+            const uint32_t prev = atomicCAS(ctr, pos, pos + 1);
+            if (prev == pos) return (long long)pos;
+            pos = prev;
+        } else if (dif < 0) {
+            return -1;
+        } else {
+            pos = ld_volatile(ctr);
+        }
+    }
+    return -1;
+}
+
+// Push a record of R words.  The source is shared memory at `src_sm` (>= 0) or global
+// memory at `src_g`; lanes < W may replace the untried-value words by `my_rem`.
+static __device__ bool q_push(Team *T, uint32_t *seq, uint32_t *rec, int src_sm, const uint32_t *src_g,
+                       int R, int S, int W, bool override_rem, uint32_t my_rem) {
+    const int lane = lane_id();
+    long long pos = -1;
+    if (lane == 0) pos = q_claim(&T->tail, seq, (uint32_t)SA.qmask, true);
+    pos = __shfl_sync(FULLMASK, pos, 0);
+    if (pos < 0) return false;
+    uint32_t *dst = rec + (size_t)((uint32_t)pos & (uint32_t)SA.qmask) * SA.rmax;
+    if (src_sm >= 0) copy_sg(dst, src_sm, R);
+    else copy_gg(dst, src_g, R);
+    __syncwarp();
+    if (override_rem && lane < W) dst[S + lane] = my_rem;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(&seq[(uint32_t)pos & (uint32_t)SA.qmask], (uint32_t)pos + 1u);
+    return true;
+}
+
+// Pop a record into shared memory at `dst`.
+static __device__ bool q_pop(Team *T, uint32_t *seq, uint32_t *rec, int dst, int R) {
+    const int lane = lane_id();
+    long long pos = -1;
+    if (lane == 0) pos = q_claim(&T->head, seq, (uint32_t)SA.qmask, false);
+    pos = __shfl_sync(FULLMASK, pos, 0);
+    if (pos < 0) return false;
+    const uint32_t slot = (uint32_t)pos & (uint32_t)SA.qmask;
+    __threadfence();
+    copy_gs_cg(dst, rec + (size_t)slot * SA.rmax, R);
+    __syncwarp();
+    __threadfence();
+    if (lane == 0) st_release(&seq[slot], (uint32_t)pos + (uint32_t)SA.qmask + 1u);
+    return true;
+}
+
+// ------------------------------------------------------------------ worker
+
+template <int W, bool ST>
+struct Worker {
+    IV<ST> I;
+    Team *T;
+    int slots;            // SM offset of the lsm stack records
+    int wso;              // SM offset of this warp's WarpShared
+    int lsm, R, S;
+    int top, base;        // open levels [0, top); levels >= base are in shared memory
+    uint32_t tick;        // nodes of this worker (low bits pace the periodic checks)
+    int gw;               // global worker index
+    int stop;             // a poll saw the stop flag
+
+    __device__ __forceinline__ WarpShared &ws() const {
+        return *reinterpret_cast<WarpShared *>(&SM[wso]);
+    }
+    __device__ __forceinline__ int chg() const { return wso; }
+    __device__ __forceinline__ int evs() const { return wso + 32; }
+    __device__ __forceinline__ uint32_t *qseq() const {
+        return SA.qseq + (SA.batch ? (size_t)blockIdx.x * (SA.qmask + 1) : 0);
+    }
+    __device__ __forceinline__ uint32_t *qrec() const {
+        return SA.qrec + (SA.batch ? (size_t)blockIdx.x * (SA.qmask + 1) * SA.rmax : 0);
+    }
+    __device__ __forceinline__ uint32_t *spill(int k) const {
+        return SA.spill + ((size_t)gw * SA.depth + k) * SA.rmax;
+    }
+    __device__ __forceinline__ int slot(int k) const { return slots + (k % lsm) * R; }
+
+    // make the shared slot of level k (== top) free
+    __device__ void make_room(int k) {
+        const int old = k - lsm;
+        if (old >= base) {
+            copy_sg(spill(old), slot(old), R);
+            __syncwarp();
+            base = old + 1;
+            if (lane_id() == 0) ws().spills++;
+        }
+    }
+    // after a pop: the new top level must be in shared memory
+    __device__ void refill() {
+        if (top > 0 && top - 1 < base) {
+            const int k = top - 1;
+            copy_gs_cg(slot(k), spill(k), R);
+            __syncwarp();
+            base = k;
+        }
+    }
+
+    // Issue the loads of the stop flags now; their value is consumed after the next node.
+    __device__ __forceinline__ int poll() const {
+        int s = 0;
+        if (lane_id() == 0) {
+            s = ld_volatile(&SA.g->abort);
+            if (SA.mode == 1) s |= ld_volatile(&T->found);
+        }
+        return s;
+    }
+
+    __device__ void check_limits() {
+        if (lane_id() == 0) {
+            if (SA.node_limit > 0) {
+                const unsigned long long tot = atomicAdd(&SA.g->node_progress, 64ull) + 64ull;
+                if ((long long)tot >= SA.node_limit) {
+                    atomicCAS(&SA.g->status, 0, CSP_ELIMIT_);
+                    atomicExch(&SA.g->abort, 1);
+                }
+            }
+            if (SA.deadline_ns > 0 && global_ns() - ws().t_start > SA.deadline_ns) {
+                atomicCAS(&SA.g->status, 0, CSP_ELIMIT_);
+                atomicExch(&SA.g->abort, 1);
+            }
+        }
+    }
+
+    __device__ void record_solution(int st) {
+        const int lane = lane_id();
+        const int n = I.n;
+        bool keep = true;
+        if (SA.mode == 1) {
+            int won = 0;
+            if (lane == 0) won = atomicCAS(&T->found, 0, 1) == 0;
+            keep = __shfl_sync(FULLMASK, won, 0) != 0;
+            stop = 1;         // this worker saw a solution: no further node in FIRST mode
+        }
+        if (!keep) return;
+        if (lane == 0) {
+            unsigned long long h = 0x9E3779B97F4A7C15ull;
+            for (int i = 0; i < n; ++i) {
+                const unsigned val = (unsigned)(I.lo0 + dom_min<W>(st + i * W));
+                h = splitmix64(h ^ (((unsigned long long)(unsigned)i << 32) | val));
+            }
+            WarpShared &w = ws();
+            w.sols++;
+            w.hsum += h;
+            w.hxor ^= h;
+        }
+        long long slot_off = -1;
+        if (SA.mode == 1) {
+            slot_off = ws().sol_off;
+        } else if (SA.cap > 0) {
+            unsigned long long s = 0;
+            if (lane == 0 && ld_volatile((const uint32_t *)&SA.g->stored) < (uint32_t)SA.cap)
+                s = atomicAdd(&SA.g->stored, 1ull) + 1ull;
+            s = __shfl_sync(FULLMASK, s, 0);
+            if (s > 0 && (long long)s <= SA.cap) slot_off = (long long)(s - 1) * n;
+        }
+        if (slot_off >= 0 && SA.sols != nullptr)
+            for (int i = lane; i < n; i += 32) SA.sols[slot_off + i] = I.lo0 + dom_min<W>(st + i * W);
+        __syncwarp();
+    }
+
+    // donate the shallowest untried values when another worker is idle
+    __device__ void donate() {
+        const int lane = lane_id();
+        for (int s = 0; s < top; ++s) {
+            const bool in_sm = s >= base;
+            uint32_t *Lg = in_sm ? nullptr : spill(s);
+            const int Ls = in_sm ? slot(s) : -1;
+            uint32_t r = 0u;
+            if (lane < W) r = in_sm ? SM[Ls + S + lane] : Lg[S + lane];
+            const int pc = __reduce_add_sync(FULLMASK, __popc(r));
+            if (pc == 0) continue;
+            if (s == top - 1 && pc < 2) return;
+            // the top level keeps its lowest value; a deeper level gives all of them away
+            uint32_t give = r;
+            if (s == top - 1) {
+                const uint32_t nz = __ballot_sync(FULLMASK, r != 0u);
+                if (lane == __ffs(nz) - 1) give = r & (r - 1);
+            }
+            if (lane == 0) atomicAdd(&T->work, 1);
+            if (q_push(T, qseq(), qrec(), Ls, Lg, R, S, W, true, give)) {
+                if (lane < W) {
+                    if (in_sm) SM[Ls + S + lane] = r & ~give;
+                    else Lg[S + lane] = r & ~give;
+                }
+                __syncwarp();
+                if (lane == 0) ws().steals++;
+            } else if (lane == 0) {
+                atomicSub(&T->work, 1);
+            }
+            return;
+        }
+    }
+
+    // propagate the node in the shared slot C of level cl; open a level on success
+    __device__ void node(int C, int cl, bool full) {
+        const int lane = lane_id();
+        tick++;
+        // loads whose latency overlaps the fixpoint: stop flags and the donation signal
+        const int p_stop = poll();
+        int p_idle = 0;
+        uint32_t p_qlen = 0;
+        const bool may_donate = !(SA.flags & F_NO_DONATE) && (tick & 7) == 0;
+        if (may_donate && lane == 0) {
+            p_idle = ld_volatile(&T->idle);
+            p_qlen = ld_volatile(&T->tail) - ld_volatile(&T->head);
+        }
+        if ((tick & 63) == 0) check_limits();
+        unsigned long long ev = 0;
+        const bool failed = fixpoint<W, ST>(I, C, chg(), evs(), full, ev);
+        if (lane == 0) {
+            WarpShared &w = ws();
+            w.nodes++;
+            w.evals += ev;
+        }
+        stop = __shfl_sync(FULLMASK, p_stop, 0);
+        if (failed) {
+            if (lane == 0) ws().fails++;
+            refill();
+            return;
+        }
+        const int y = select_first_fail<W>(C, I.n);
+        if (y < 0) {
+            record_solution(C);
+            refill();
+            return;
+        }
+        if (lane < W) SM[C + S + lane] = SM[C + y * W + lane];
+        if (lane == 0) SM[C + S + W] = (uint32_t)y;
+        __syncwarp();
+        top = cl + 1;
+        if (lane == 0 && top > ws().maxd) ws().maxd = top;
+        const int want = __shfl_sync(FULLMASK, (p_idle > 0 && (int)p_qlen < p_idle) ? 1 : 0, 0);
+        if (want) donate();
+    }
+
+    // child of the top level: next value of its branching variable (the level is popped
+    // when it has none left)
+    __device__ void expand() {
+        const int lane = lane_id();
+        const int p = top - 1;
+        const int P = slot(p);
+        const uint32_t r = lane < W ? SM[P + S + lane] : 0u;
+        const uint32_t nz = __ballot_sync(FULLMASK, r != 0u);
+        if (!nz) {
+            top = p;
+            refill();
+            return;
+        }
+        const int k = __ffs(nz) - 1;
+        const uint32_t rw = __shfl_sync(FULLMASK, r, k);
+        const int v = (k << 5) + __ffs(rw) - 1;
+        const uint32_t rest = rw & (rw - 1);
+        const bool last = rest == 0u && (nz & ~(1u << k)) == 0u;
+        const int x = (int)SM[P + S + W];
+        int C, cl;
+        __syncwarp();
+        if (last) {
+            cl = p;
+            C = P;
+            top = p;          // the level is consumed; its slot becomes the child
+        } else {
+            if (lane == k) SM[P + S + k] = rest;
+            cl = p + 1;
+            make_room(cl);
+            C = slot(cl);
+            __syncwarp();
+            copy_ss(C, P, R);
+        }
+        __syncwarp();
+        if (lane < W) SM[C + x * W + lane] = (lane == (v >> 5)) ? (1u << (v & 31)) : 0u;
+        if (lane < I.NW) SM[chg() + lane] = (lane == (x >> 5)) ? (1u << (x & 31)) : 0u;
+        __syncwarp();
+        node(C, cl, false);
+    }
+
+    // run the record now in slot 0 to exhaustion
+    __device__ void explore() {
+        base = 0;
+        top = 0;
+        stop = __shfl_sync(FULLMASK, poll(), 0);
+        if (stop) return;
+        const int var = (int)SM[slots + S + W];
+        if (var < 0) node(slots, 0, true);
+        else top = 1;
+        while (top > 0) {
+            if (stop) { top = 0; break; }
+            expand();
+        }
+    }
+
+    // take records until the team has no work left
+    __device__ void run() {
+        const int lane = lane_id();
+        for (;;) {
+            if (lane == 0) atomicAdd(&T->idle, 1);
+            const long long t0 = global_ns();
+            int got = 0;
+            unsigned sleep = 32;
+            for (;;) {
+                if (q_pop(T, qseq(), qrec(), slots, R)) { got = 1; break; }
+                int done = 0;
+                if (lane == 0) {
+                    if (ld_volatile(&T->work) == 0 || ld_volatile(&SA.g->abort)) done = 1;
+                    else if (global_ns() - t0 > SA.wait_limit_ns) {
+                        atomicCAS(&SA.g->status, 0, CSP_ETIMEOUT_);
+                        atomicExch(&SA.g->abort, 1);
+                        done = 1;
+                    }
+                }
+                if (__shfl_sync(FULLMASK, done, 0)) break;
+                __nanosleep(sleep);
+                sleep = sleep < 4096 ? sleep * 2 : 4096;
+            }
+            if (lane == 0) atomicSub(&T->idle, 1);
+            if (!got) return;
+            explore();
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicSub(&T->work, 1);
+            }
+        }
+    }
+
+    __device__ void init_shared() {
+        if (lane_id() == 0) {
+            WarpShared &w = ws();
+            w.nodes = w.fails = w.sols = w.hsum = w.hxor = 0;
+            w.evals = w.steals = w.spills = 0;
+            w.maxd = 0;
+            w.sol_off = 0;
+            w.t_start = global_ns();
+        }
+        __syncwarp();
+    }
+
+    __device__ void flush() {
+        if (lane_id() == 0) {
+            GState *g = SA.g;
+            WarpShared &w = ws();
+            atomicAdd(&g->nodes, w.nodes);
+            atomicAdd(&g->fails, w.fails);
+            atomicAdd(&g->solutions, w.sols);
+            atomicAdd(&g->hsum, w.hsum);
+            atomicXor(&g->hxor, w.hxor);
+            atomicAdd(&g->evals, w.evals);
+            atomicAdd(&g->steals, w.steals);
+            atomicAdd(&g->spills, w.spills);
+            atomicMax(&g->max_depth, w.maxd);
+        }
+    }
+};
+
+// stage an instance's constraint words into SM[0..) (whole block)
+__device__ __forceinline__ void stage_instance(const uint32_t *ib) {
+    const int words = ((int)ib[H_CONS_WORDS] + 3) & ~3;
+    const uint4 *s = reinterpret_cast<const uint4 *>(ib);
+    uint4 *d = reinterpret_cast<uint4 *>(SM);
+    for (int i = threadIdx.x; i < words / 4; i += blockDim.x) d[i] = s[i];
+}
+
+template <int W, bool ST>
+#ifndef CUBICS_SEARCH_MINB
+#define CUBICS_SEARCH_MINB 1
+#endif
+__global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const SearchArgs Ap) {
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    __shared__ int s_inst;
+    __shared__ unsigned long long s_nodes, s_fails, s_sols;
+    if (threadIdx.x == 0) SA = Ap;
+    __syncthreads();
+    const int per_warp = SA.lsm * SA.rmax + WS_WORDS;
+
+    Worker<W, ST> wk;
+    wk.lsm = SA.lsm;
+    wk.slots = SA.stage_words + warp * per_warp;
+    wk.wso = wk.slots + SA.lsm * SA.rmax;
+    wk.gw = blockIdx.x * SA.warps + warp;
+    wk.tick = 0;
+    wk.stop = 0;
+    wk.init_shared();
+
+    if (!SA.batch) {
+        const uint32_t *ib = SA.arena + SA.inst_off[0];
+        if (ST) stage_instance(ib);
+        __syncthreads();
+        wk.I.load(ib);
+        wk.S = wk.I.S;
+        wk.R = record_words(wk.S, W);
+        wk.T = SA.teams;
+        wk.run();
+        wk.flush();
+        return;
+    }
+
+    Team *T = SA.teams + blockIdx.x;
+    wk.T = T;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_inst = ld_volatile(&SA.g->abort) ? SA.n_inst : atomicAdd(&SA.g->ticket, 1);
+            s_nodes = 0;
+            s_fails = 0;
+            s_sols = 0;
+        }
+        __syncthreads();
+        const int i = s_inst;
+        if (i >= SA.n_inst) break;
+        const uint32_t *ib = SA.arena + SA.inst_off[i];
+        if (ST) stage_instance(ib);
+        __syncthreads();
+        wk.I.load(ib);
+        wk.S = wk.I.S;
+        wk.R = record_words(wk.S, W);
+        const unsigned long long n0 = wk.ws().nodes, f0 = wk.ws().fails, s0 = wk.ws().sols;
+        if (lane == 0) wk.ws().sol_off = SA.sol_off ? SA.sol_off[i] : 0;
+        __syncwarp();
+        if (warp == 0) {
+            if (lane == 0) {
+                T->found = 0;
+                T->work = 1;
+                T->inst = i;
+            }
+            // root record: the instance's root domains, nothing to try yet, var = -1
+            const uint32_t *root = ib + ib[H_OFF_ROOT];
+            for (int k = lane; k < wk.R; k += 32)
+                SM[wk.slots + k] = k < wk.S ? root[k] : (k == wk.S + W ? 0xffffffffu : 0u);
+            __syncwarp();
+            __threadfence();
+            q_push(T, wk.qseq(), wk.qrec(), wk.slots, nullptr, wk.R, wk.S, W, false, 0u);
+        }
+        __syncthreads();
+        wk.run();
+        if (lane == 0) {
+            atomicAdd(&s_nodes, wk.ws().nodes - n0);
+            atomicAdd(&s_fails, wk.ws().fails - f0);
+            atomicAdd(&s_sols, wk.ws().sols - s0);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            InstResult &r = SA.results[i];
+            const int st = ld_volatile(&SA.g->status);
+            r.status = T->found || s_sols > 0 ? 1 : (st != 0 ? st : 0);
+            r.n = (int)ib[H_N];
+            r.nodes = s_nodes;
+            r.fails = s_fails;
+            r.solutions = s_sols;
+            r.sol_offset = SA.sol_off ? SA.sol_off[i] : 0;
+        }
+        __syncthreads();
+    }
+    wk.flush();
+}
+
+// ------------------------------------------------------------------ propagate kernel
+
+template <int W, bool ST>
+__global__ void __launch_bounds__(256) propagate_kernel(PropArgs P) {
+    if (ST) stage_instance(P.inst);
+    __syncthreads();
+    IV<ST> I;
+    I.load(P.inst);
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int warps = blockDim.x >> 5;
+    const int S4 = (I.S + 3) & ~3;
+    const int dom = P.stage_words + warp * (S4 + 64);
+    const int chg = dom + S4, evs = chg + 32;
+    unsigned long long evals = 0;
+    for (int s = blockIdx.x * warps + warp; s < P.count; s += gridDim.x * warps) {
+        const uint32_t *src = P.din + (size_t)s * I.S;
+        for (int k = lane; k < I.S; k += 32) SM[dom + k] = src[k];
+        __syncwarp();
+        const bool failed = fixpoint<W, ST>(I, dom, chg, evs, true, evals);
+        __syncwarp();
+        uint32_t *dst = P.dout + (size_t)s * I.S;
+        for (int k = lane; k < I.S; k += 32) dst[k] = SM[dom + k];
+        if (lane == 0) P.failed[s] = failed ? 1 : 0;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ host launchers
+
+template <int W, bool ST>
+cudaError_t launch_search_t(const SearchArgs &A, int blocks, int threads, size_t smem,
+                            cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<W, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    search_kernel<W, ST><<<blocks, threads, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <int W, bool ST>
+cudaError_t occupancy_t(int threads, size_t smem, int *bps) {
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<W, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, search_kernel<W, ST>, threads, smem);
+}
+
+template <int W, bool ST>
+cudaError_t launch_prop_t(const PropArgs &P, int blocks, int threads, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(propagate_kernel<W, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    propagate_kernel<W, ST><<<blocks, threads, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+// one translation unit per W defines these for both staging modes
+#define CUBICS_DEFINE_WIDTH(WW)                                                              \
+    cudaError_t launch_search_w##WW(bool st_, const SearchArgs &A, int b, int t, size_t sm, \
+                                    cudaStream_t s) {                                       \
+        return st_ ? launch_search_t<WW, true>(A, b, t, sm, s)                              \
+                   : launch_search_t<WW, false>(A, b, t, sm, s);                            \
+    }                                                                                       \
+    cudaError_t occupancy_w##WW(bool st_, int t, size_t sm, int *bps) {                     \
+        return st_ ? occupancy_t<WW, true>(t, sm, bps) : occupancy_t<WW, false>(t, sm, bps); \
+    }                                                                                       \
+    cudaError_t launch_prop_w##WW(bool st_, const PropArgs &P, int b, int t, size_t sm,     \
+                                  cudaStream_t s) {                                         \
+        return st_ ? launch_prop_t<WW, true>(P, b, t, sm, s)                                \
+                   : launch_prop_t<WW, false>(P, b, t, sm, s);                              \
+    }
+
+}  // namespace cubics

@@ -42,7 +42,8 @@ class csp_stats_t(C.Structure):
                 ("sol_hash_sum", C.c_uint64), ("sol_hash_xor", C.c_uint64),
                 ("prop_evals", C.c_uint64), ("steals", C.c_uint64), ("spills", C.c_uint64),
                 ("max_depth", C.c_int32), ("status", C.c_int32), ("ms", C.c_double),
-                ("stored", C.c_int64), ("workers", C.c_int32), ("blocks", C.c_int32)]
+                ("stored", C.c_int64), ("workers", C.c_int32), ("blocks", C.c_int32),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
 
 
 class csp_result(C.Structure):
@@ -82,6 +83,7 @@ SIGNATURES = {
     "csp_batch_solution_words": (C.c_int64, [_VP]),
     "csp_batch_stats": (C.c_int, [_VP, C.POINTER(csp_stats_t)]),
     "csp_batch_destroy": (None, [_VP]),
+    "csp_probe_smem_bandwidth": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -254,6 +256,16 @@ class Csp:
 
 
 # ----------------------------------------------------------------------------- batches
+
+def probe_smem_bandwidth(stream=None, reps: int = 10) -> float:
+    """Measured shared-memory read bandwidth of the current device in GB/s."""
+    import torch
+    out = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    g = C.c_double()
+    _check(lib().csp_probe_smem_bandwidth(C.c_void_p(out.data_ptr()), _stream_handle(stream),
+                                          reps, C.byref(g)), "csp_probe_smem_bandwidth")
+    return g.value
+
 
 class Batch:
     """Many CSPs solved by one persistent launch (csp_batch_*)."""

@@ -212,6 +212,27 @@ def test_first_mode_single_worker_is_the_oracle_order():
             assert tuple(sols[0]) == tuple(r.sols[0])
 
 
+def oracle_reference(N):
+    """Full-size oracle results written by tests/golden/make_queens_reference.py."""
+    path = os.path.join(GOLDEN, "queens_oracle.txt")
+    for ln in open(path):
+        if ln.strip() and not ln.startswith("#"):
+            f = list(map(int, ln.split()[:6]))
+            if f[0] == N:
+                return dict(zip(["N", "nodes", "fails", "solutions", "hash_sum", "hash_xor"], f))
+    pytest.skip(f"no oracle reference for N={N}")
+
+
+@pytest.mark.parametrize("N", [14, 16])
+def test_queens_full_size_against_oracle_reference(N):
+    ref = oracle_reference(N)
+    p = K.Csp(I.queens(N))
+    rc, st, _ = p.solve(K.CSP_ALL, 0)
+    assert rc == 0 and st["solutions"] == queens_count(N) == ref["solutions"]
+    assert (st["nodes"], st["fails"]) == (ref["nodes"], ref["fails"])
+    assert (st["sol_hash_sum"], st["sol_hash_xor"]) == (ref["hash_sum"], ref["hash_xor"])
+
+
 def test_queens_14_full_size():
     p = K.Csp(I.queens(14))
     rc, st, _ = p.solve(K.CSP_ALL, 0)
