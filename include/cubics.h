@@ -84,6 +84,7 @@ typedef struct {
     int32_t blocks;          /* blocks of the last launch */
     int64_t h2d_bytes;       /* host-to-device bytes of the last upload */
     int64_t d2h_bytes;       /* device-to-host bytes of the last collect */
+    uint64_t wait_ns;        /* summed over workers: time spent waiting for work */
 } csp_stats_t;
 
 typedef struct {

@@ -350,6 +350,7 @@ void fill_stats(csp_stats_t *s, const GState &g, int64_t stored) {
     s->spills = g.spills;
     s->max_depth = g.max_depth;
     s->stored = stored;
+    s->wait_ns = g.wait_ns;
 }
 
 }  // namespace

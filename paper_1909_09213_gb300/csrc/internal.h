@@ -51,11 +51,12 @@ struct GState {               // counters of one launch
     unsigned long long nodes, fails, solutions, hsum, hxor, evals, steals, spills;
     unsigned long long stored;        // solution slots taken
     unsigned long long node_progress; // for the node limit
+    unsigned long long wait_ns;       // summed over workers: time spent waiting for work
     int32_t max_depth;
     int32_t status;                   // 0 ok, else CSP_E*
     int32_t abort;                    // global stop
     int32_t ticket;                   // next batch instance
-    int32_t pad[24];
+    int32_t pad[22];
 };
 
 struct InstResult {

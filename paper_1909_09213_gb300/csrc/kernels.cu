@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(1024) smem_probe_kernel(uint4 *out, int iters)
 #pragma unroll 8
     for (int it = 0; it < iters; ++it) {
         uint32_t x, y, z, w;
-        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+        // volatile: every iteration issues its load (the addresses repeat every 4 iterations)
+        asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(x), "=r"(y), "=r"(z), "=r"(w)
                      : "r"(base + 16u * (uint32_t)idx));
         a ^= x; b ^= y; c ^= z; d ^= w;

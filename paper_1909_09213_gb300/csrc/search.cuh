@@ -33,7 +33,8 @@ struct WarpShared {
     unsigned long long nodes, fails, sols, hsum, hxor, evals, steals, spills;
     long long t_start;
     int64_t sol_off;
-    int32_t maxd, pad[3];
+    long long wait_ns;    // time spent waiting for a record
+    int32_t maxd, pad;
 };
 static_assert(sizeof(WarpShared) == 4 * WS_WORDS, "WarpShared size must match WS_WORDS");
 
@@ -363,7 +364,10 @@ struct Worker {
                 __nanosleep(sleep);
                 sleep = sleep < 4096 ? sleep * 2 : 4096;
             }
-            if (lane == 0) atomicSub(&T->idle, 1);
+            if (lane == 0) {
+                atomicSub(&T->idle, 1);
+                ws().wait_ns += global_ns() - t0;
+            }
             if (!got) return;
             explore();
             __syncwarp();
@@ -381,6 +385,7 @@ struct Worker {
             w.evals = w.steals = w.spills = 0;
             w.maxd = 0;
             w.sol_off = 0;
+            w.wait_ns = 0;
             w.t_start = global_ns();
         }
         __syncwarp();
@@ -398,6 +403,7 @@ struct Worker {
             atomicAdd(&g->evals, w.evals);
             atomicAdd(&g->steals, w.steals);
             atomicAdd(&g->spills, w.spills);
+            atomicAdd(&g->wait_ns, (unsigned long long)w.wait_ns);
             atomicMax(&g->max_depth, w.maxd);
         }
     }
