@@ -28,7 +28,7 @@ METRIC = "search nodes propagated/sec and time-to-all/first-solution vs plain GP
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE = os.path.join(ROOT, "profiles", "search_kernel_queens16.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_09213_gb300", "csrc", f)
-                  for f in ("kernels.cu", "device.cuh", "internal.h")]
+                  for f in ("search.cuh", "device.cuh", "internal.h", "kernels_w1.cu")]
 
 
 def kernel_digest() -> str:
