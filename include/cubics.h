@@ -194,6 +194,35 @@ int64_t csp_batch_solution_words(const csp_batch_t *b);
 int csp_batch_stats(const csp_batch_t *b, csp_stats_t *out);
 void csp_batch_destroy(csp_batch_t *b);
 
+/* ---------------------------------------------------------------- allocation-free search */
+
+/* csp_solve for callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is unavailable or forbidden (a caller inside a stream capture that must not
+ * allocate, a plug-in whose host application owns every allocation, a real-time loop that
+ * may not block in the allocator).  The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * Instead of a bound workspace, the search uses a scratch array inside the library's own
+ * device image (CSP_NOALLOC_SCRATCH_BYTES = 16 MiB, reserved on every GPU that loads the
+ * library until the process exits).  The call performs no cudaMalloc, cudaFree,
+ * cudaMallocHost or other device/pinned allocation: the encoded problem is copied from
+ * ordinary host memory straight into the array, and results are copied back the same way.
+ * Inputs and outputs are the caller's: the handle h (model built with csp_create/post),
+ * sol_out (host, cap * n int32; may be NULL when cap == 0) and the statistics read back
+ * with csp_stats (stats.ms is 0: no events are created).  cuda_stream: cudaStream_t as
+ * void* (NULL = legacy stream); the call is synchronous on it.
+ *
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * on a device shares the one array and leaves its contents behind; the counters that must
+ * start at zero are cleared by each call.  Calls that overlap on the GPU (other host
+ * threads, other streams) race on the array: serialise them.  Returns CSP_ENOMEM when the
+ * problem, the launch shape (csp_set_tiling) and cap need more than the array holds, plus
+ * the error codes of csp_solve. */
+#define CSP_NOALLOC_SCRATCH_BYTES (16u << 20)
+int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
+                      const csp_limits *lim, void *cuda_stream);
+
 /* ---------------------------------------------------------------- measurement */
 
 /* Shared-memory bandwidth of the current device (a measurement helper with no counterpart

@@ -949,6 +949,93 @@ int csp_probe_smem_bandwidth(void *dev_out, void *cuda_stream, int32_t reps, dou
     return cuda_status(probe_smem(dev_out, (cudaStream_t)cuda_stream, di.sms, reps, gbs));
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------- no-alloc search
+
+namespace {
+
+// Scratch of csp_solve_noalloc, part of the library's device image: every GPU that loads
+// the library holds these bytes until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CSP_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address of the array, per device
+
+}  // namespace
+
+extern "C" {
+
+int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
+                      const csp_limits *lim, void *cuda_stream) {
+    if (!h || mode < 0 || mode > 1 || cap < 0 || cap > INT32_MAX) return CSP_EINVAL;
+    if (cap > 0 && !sol_out) return CSP_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return CSP_ECUDA; }
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return CSP_ECUDA;
+    if (!g_noalloc_ptr[dev]) {
+        // set-up, once per device with that device current: the host-side name of the
+        // array is not a device address, so look the address up
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return CSP_ECUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    // lay the search out in the array as it would be in a bound workspace
+    uint8_t *const saved_ws = h->ws;
+    const size_t saved_bytes = h->ws_bytes;
+    const cudaStream_t saved_stream = h->stream;
+    size_t need = 0;
+    int rc = plan_single(h, mode, cap, &need, &h->block);
+    if (rc) return rc;
+    if (need > (size_t)CSP_NOALLOC_SCRATCH_BYTES) return CSP_ENOMEM;
+    h->ws = (uint8_t *)g_noalloc_ptr[dev];
+    h->ws_bytes = CSP_NOALLOC_SCRATCH_BYTES;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->uploaded = false;
+    const int64_t zero = 0;
+    SearchArgs A = single_args(h, mode, cap, lim);
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, h->block.data(), h->block.size() * 4,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ws + h->o_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_g, 0, sizeof(GState), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_team, 0, sizeof(Team), h->stream);
+    if (e == cudaSuccess) e = launch_init_single(A, h->stream);
+    if (e == cudaSuccess)
+        e = launch_search(h->W, h->shape.stage_words > 0, A, h->shape.blocks, h->shape.warps * 32,
+                          h->shape.smem, h->stream);
+    GState g;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&g, h->ws + h->o_g, sizeof(g), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    int64_t stored = 0;
+    if (e == cudaSuccess) {
+        const int64_t c1 = mode == CSP_FIRST ? 1 : cap;
+        stored = std::min<int64_t>(mode == CSP_ALL ? (int64_t)g.stored : (int64_t)g.solutions, c1);
+        if (sol_out && stored > 0) {
+            e = cudaMemcpyAsync(sol_out, h->ws + h->o_sols, (size_t)stored * h->n * 4,
+                                cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        }
+    }
+    h->ws = saved_ws;
+    h->ws_bytes = saved_bytes;
+    h->stream = saved_stream;
+    h->uploaded = false;
+    if (e != cudaSuccess) return cuda_status(e);
+    fill_stats(&h->stats, g, stored);
+    h->stats.ms = 0.0;
+    h->stats.status = g.status;
+    h->stats.workers = h->shape.blocks * h->shape.warps;
+    h->stats.blocks = h->shape.blocks;
+    h->stats.h2d_bytes = (int64_t)h->block.size() * 4 + (int64_t)sizeof(int64_t);
+    h->stats.d2h_bytes = (int64_t)sizeof(GState) + stored * h->n * 4;
+    return g.status;
+}
+
 const char *csp_strerror(int code) {
     switch (code) {
     case CSP_OK: return "ok";

@@ -84,6 +84,7 @@ SIGNATURES = {
     "csp_batch_stats": (C.c_int, [_VP, C.POINTER(csp_stats_t)]),
     "csp_batch_destroy": (None, [_VP]),
     "csp_probe_smem_bandwidth": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_double)]),
+    "csp_solve_noalloc": (C.c_int, [_VP, C.c_int32, C.c_int64, _I32P, C.POINTER(csp_limits), _VP]),
 }
 
 _lib = None
