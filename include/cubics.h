@@ -146,6 +146,14 @@ int csp_workspace_bytes(const csp_t *h, int32_t mode, int64_t cap, size_t *bytes
  * them alive until the handle is destroyed or rebound. */
 int csp_bind(csp_t *h, void *dev, size_t bytes, void *cuda_stream);
 
+/* Share one search tree between nparts ranks (search-space partitioning, Section 1.3): the
+ * root is propagated by every rank, and its children (the values of the root's branching
+ * variable, ascending) are dealt round-robin, rank `part` exploring positions
+ * part, part + nparts, ...  The root's own node, fail or solution is counted by part 0 only,
+ * so summing the ranks' counts and hash sums (and xoring their hash xors) gives the
+ * undivided search's results.  Default 0 of 1.  CSP_EINVAL unless 0 <= part < nparts. */
+int csp_set_partition(csp_t *h, int32_t part, int32_t nparts);
+
 /* Branching heuristic: CSP_BR_FIRST_FAIL (smallest domain, lowest index) or
  * CSP_BR_LEARNED with the brancher's bf16 weights (host array, csp_brancher_params()
  * values; NULL keeps the loaded weights).  Learned ordering changes only exploration order. */

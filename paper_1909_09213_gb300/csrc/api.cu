@@ -125,6 +125,7 @@ struct csp {
     int32_t lo0 = 0, W = 1;
     csp_tiling tiling{0, 0, 0, 0};
     int32_t brancher = CSP_BR_FIRST_FAIL;
+    int32_t part = 0, nparts = 1;    // root children dealt round-robin across ranks
     // device binding
     uint8_t *ws = nullptr;
     size_t ws_bytes = 0;
@@ -336,6 +337,8 @@ SearchArgs single_args(csp *h, int32_t mode, int64_t cap, const csp_limits *lim)
     A.deadline_ns = lim ? lim->time_limit_ns : 0;
     A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
     A.mlp = nullptr;
+    A.part = h->part;
+    A.nparts = h->nparts;
     return A;
 }
 
@@ -469,6 +472,13 @@ int csp_set_tiling(csp_t *h, const csp_tiling *t) {
         return CSP_EINVAL;
     }
     invalidate(h);
+    return CSP_OK;
+}
+
+int csp_set_partition(csp_t *h, int32_t part, int32_t nparts) {
+    if (!h || nparts < 1 || part < 0 || part >= nparts) return CSP_EINVAL;
+    h->part = part;
+    h->nparts = nparts;
     return CSP_OK;
 }
 
@@ -734,6 +744,8 @@ SearchArgs batch_args(csp_batch *b, const csp_limits *lim) {
     A.deadline_ns = lim ? lim->time_limit_ns : 0;
     A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
     A.mlp = nullptr;
+    A.part = 0;
+    A.nparts = 1;
     return A;
 }
 

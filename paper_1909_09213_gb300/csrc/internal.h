@@ -80,6 +80,7 @@ struct SearchArgs {
     int32_t qmask;            // queue capacity - 1
     int32_t flags;
     int32_t warps;            // workers per block
+    int32_t part, nparts;     // single mode: explore only the root children of rank part
     GState *g;
     Team *teams;
     uint32_t *qseq;           // per team: qcap sequence words

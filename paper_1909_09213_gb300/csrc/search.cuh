@@ -260,24 +260,43 @@ struct Worker {
         if ((tick & 63) == 0) check_limits();
         unsigned long long ev = 0;
         const bool failed = fixpoint<W, ST>(I, C, chg(), evs(), full, ev);
-        if (lane == 0) {
+        // a root shared by several ranks (its children dealt round-robin) counts on rank 0 only
+        const bool split_root = full && !SA.batch && SA.nparts > 1;
+        const bool counted = !split_root || SA.part == 0;
+        if (lane == 0 && counted) {
             WarpShared &w = ws();
             w.nodes++;
             w.evals += ev;
         }
         stop = __shfl_sync(FULLMASK, p_stop, 0);
         if (failed) {
-            if (lane == 0) ws().fails++;
+            if (lane == 0 && counted) ws().fails++;
             refill();
             return;
         }
         const int y = select_first_fail<W>(C, I.n);
         if (y < 0) {
-            record_solution(C);
+            if (counted) record_solution(C);
             refill();
             return;
         }
-        if (lane < W) SM[C + S + lane] = SM[C + y * W + lane];
+        uint32_t rw = lane < W ? SM[C + y * W + lane] : 0u;
+        if (split_root) {
+            // keep the values whose position in D(y), ascending, is part mod nparts
+            uint32_t before = 0;
+            for (int k = 0; k < W; ++k) {
+                const uint32_t pk = __shfl_sync(FULLMASK, (uint32_t)__popc(rw), k);
+                if (k < lane) before += pk;
+            }
+            uint32_t keep = 0;
+            for (uint32_t m = rw; m; m &= m - 1) {
+                const uint32_t bit = m & (~m + 1u);
+                const uint32_t pos = before + (uint32_t)__popc(rw & (bit - 1u));
+                if (pos % (uint32_t)SA.nparts == (uint32_t)SA.part) keep |= bit;
+            }
+            rw = keep;
+        }
+        if (lane < W) SM[C + S + lane] = rw;
         if (lane == 0) SM[C + S + W] = (uint32_t)y;
         __syncwarp();
         top = cl + 1;

@@ -64,6 +64,7 @@ SIGNATURES = {
     "csp_workspace_bytes": (C.c_int, [_VP, C.c_int32, C.c_int64, C.POINTER(C.c_size_t)]),
     "csp_bind": (C.c_int, [_VP, _VP, C.c_size_t, _VP]),
     "csp_set_brancher": (C.c_int, [_VP, C.c_int32, _U16P]),
+    "csp_set_partition": (C.c_int, [_VP, C.c_int32, C.c_int32]),
     "csp_solve": (C.c_int, [_VP, C.c_int32, C.c_int64, _I32P, C.POINTER(csp_limits)]),
     "csp_upload": (C.c_int, [_VP, C.c_int32, C.c_int64]),
     "csp_launch": (C.c_int, [_VP, C.POINTER(csp_limits)]),
@@ -201,6 +202,9 @@ class Csp:
 
     def set_tiling(self, t: csp_tiling | None):
         _check(lib().csp_set_tiling(self.h, C.byref(t) if t is not None else None), "csp_set_tiling")
+
+    def set_partition(self, part: int, nparts: int):
+        _check(lib().csp_set_partition(self.h, part, nparts), "csp_set_partition")
 
     def workspace_bytes(self, mode: int, cap: int) -> int:
         b = C.c_size_t()

@@ -252,6 +252,27 @@ def test_queens_16_full_size_and_sampled_subtrees():
         search_parity(m, cap=0)
 
 
+@pytest.mark.parametrize("nparts", [2, 3, 5])
+def test_partitioned_tree_sums_to_the_whole(nparts):
+    """The parts of a shared tree (csp_set_partition), run one after another on this GPU,
+    combine to the undivided search: what ranks on separate GPUs would exchange."""
+    from paper_1909_09213_gb300 import shard
+    for m in [I.queens(12), I.model_rb(I.seed_for(I.CFG_RB, 11), 14, 7), mixed_model(210, 40, 5)]:
+        whole = K.Csp(m)
+        rc, st_whole, _ = whole.solve(K.CSP_ALL, 0)
+        assert rc == 0
+        parts = []
+        for part in range(nparts):
+            p = K.Csp(m)
+            p.set_partition(part, nparts)
+            rc, st, _ = p.solve(K.CSP_ALL, 0)
+            assert rc == 0
+            parts.append(st)
+        got = shard.combine(parts)
+        for k in shard.FIELDS:
+            assert got[k] == st_whole[k], (m.name, k)
+
+
 # ----------------------------------------------------------------------------- limits, errors
 
 def test_node_limit():
