@@ -2,9 +2,15 @@
 """Benchmark of the CUBICS hot path: search nodes propagated per second.
 
 A step is one complete search of the workload (every node labelled, propagated to its
-fixpoint and backtracked on the GPU).  Default workload: 16-queens, all solutions (the
-N-queens configuration at N = 16: 16 variables, 360 int_ne constraints, one uint32 word
-per domain).  Prints one JSON line.
+fixpoint and backtracked on the GPU).  Workloads:
+
+* queens16 (default) / queens14: N-queens, all solutions (N vars, 3 C(N,2) int_ne, one uint32
+  word per domain), one problem per step;
+* rb4096: 4096 seeded model-RB instances (n ~ U[20,60], d ~ U[8,32], tables), first solution
+  or UNSAT proof for each, all in one persistent launch replayed from a CUDA graph, with the
+  launch shape chosen by the autotuner.
+
+Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload queens16|queens14|rb4096]
   python bench.py --impl reference      # the CPU oracle on a bounded sample of the workload
@@ -25,8 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "search nodes propagated/sec and time-to-all/first-solution vs plain GPU first-fail"
-PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-PROFILE = os.path.join(ROOT, "profiles", "search_kernel_queens16.md")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_09213_gb300", "csrc", f)
                   for f in ("search.cuh", "device.cuh", "internal.h", "kernels_w1.cu")]
 
@@ -38,36 +43,14 @@ def kernel_digest() -> str:
     return h.hexdigest()[:12]
 
 
-def golden_row(N):
-    path = os.path.join(ROOT, "tests", "golden", "queens_oracle.txt")
+def traffic_from_profile(name):
+    """DRAM bytes per search launch from a committed ncu summary, if it was taken on the
+    current kernel sources."""
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
-    for ln in open(path):
-        if ln.strip() and not ln.startswith("#"):
-            f = ln.split()
-            if int(f[0]) == N:
-                return {"nodes": int(f[1]), "fails": int(f[2]), "solutions": int(f[3]),
-                        "hash_sum": int(f[4]), "hash_xor": int(f[5]), "ne_evals": int(f[6]),
-                        "work_bytes": float(f[7])}
-    return None
-
-
-def bytes_per_node(N):
-    """Algorithmic bytes per search node: read the parent state and write the child
-    (2 n W 4 bytes) plus 12 B per int_ne wake of the oracle's event-driven fixpoint."""
-    g = golden_row(N)
-    if g is None:
-        return None
-    return 2 * N * 1 * 4 + g["work_bytes"] / g["nodes"]
-
-
-def traffic_from_profile():
-    """DRAM bytes per search launch from the committed ncu summary, if it was taken on the
-    current kernel sources."""
-    if not os.path.exists(PROFILE):
-        return None
     vals = {}
-    for ln in open(PROFILE):
+    for ln in open(path):
         if ln.startswith("- ") and ":" in ln:
             k, v = ln[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
@@ -89,6 +72,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.out = ""
 
     def __enter__(self):
         try:
@@ -101,7 +85,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.out = ""
         if self.proc is not None:
             time.sleep(0.25)
             self.proc.terminate()
@@ -134,30 +117,209 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workloads
 
+class Queens:
+    """N-queens, all solutions: one problem per step."""
+
+    def __init__(self, N):
+        from paper_1909_09213_gb300 import instances as I
+        self.N = N
+        self.model = I.queens(N)
+        self.desc = (f"{N}-queens, all solutions ({N} vars, {len(self.model.ne)} int_ne, "
+                     "1 uint32 word per domain)")
+        self.profile = f"search_kernel_queens{N}.md"
+
+    def golden(self):
+        path = os.path.join(GOLDEN, "queens_oracle.txt")
+        for ln in open(path):
+            if ln.strip() and not ln.startswith("#"):
+                f = ln.split()
+                if int(f[0]) == self.N:
+                    return {"nodes": int(f[1]), "fails": int(f[2]), "solutions": int(f[3]),
+                            "hash_sum": int(f[4]), "hash_xor": int(f[5]), "work_bytes": float(f[7])}
+        return None
+
+    def bytes_per_node(self):
+        """2 n W 4 (read the parent record's domains, write the child's) + 12 B per int_ne wake
+        of the oracle's event-driven fixpoint, from the full-size oracle run."""
+        g = self.golden()
+        return None if g is None else 2 * self.N * 4 + g["work_bytes"] / g["nodes"]
+
+    def setup(self, K, stream):
+        self.p = K.Csp(self.model)
+        self.p.stream = stream
+        self.p.bind(K.CSP_ALL, 0, stream)
+        self.p.upload(K.CSP_ALL, 0)
+
+    def launch(self, K):
+        self.p.launch()
+
+    def collect(self, K):
+        rc = self.p.collect()
+        if rc != 0:
+            raise RuntimeError(f"search failed: {rc}")
+        return self.p.stats()
+
+    def e2e_step(self, K):
+        rc, st, _ = self.p.solve(K.CSP_ALL, 0)
+        return st
+
+    def parity(self, st):
+        g = self.golden()
+        if g is None:
+            return None
+        return (st["nodes"], st["fails"], st["solutions"], st["sol_hash_sum"], st["sol_hash_xor"]) == (
+            g["nodes"], g["fails"], g["solutions"], g["hash_sum"], g["hash_xor"])
+
+    def extra(self, K, st):
+        return {"solutions_per_step": st["solutions"],
+                "time_to_all_solutions_ms": st["ms"]}
+
+    def oracle_sample(self, depth):
+        """The subtree under x0=0, x1=2 (, x2=4): a bounded piece of the same search."""
+        from oracle import oracle as O
+        from paper_1909_09213_gb300 import instances as I
+        m = I.queens(self.N)
+        fixed = [(0, 0), (1, 2), (2, 4)][:depth]
+        for (v, a) in fixed:
+            m.removed += [(v, u) for u in range(self.N) if u != a]
+        t = time.perf_counter()
+        r = O.solve(O.OracleModel(m), variant=1, W=1)
+        dt = time.perf_counter() - t
+        return r.nodes, dt, f"{self.N}-queens subtree " + ", ".join(f"x{v}={a}" for v, a in fixed)
+
+    def cpu_sample(self):
+        return self.oracle_sample(2)
+
+    def reference_step(self):
+        return self.oracle_sample(3)
+
+
+class RBBatch:
+    """4096 model-RB instances, first solution or UNSAT proof each, one launch per step."""
+
+    def __init__(self, count=4096):
+        from paper_1909_09213_gb300 import instances as I
+        self.count = count
+        self.models = I.rb_batch(count)
+        self.desc = (f"{count} model-RB instances, n~U[20,60], d~U[8,32], alpha 0.8, r 0.7, "
+                     f"p {I.rb_tightness():.6f}, first solution or UNSAT each, one launch (CUDA graph)")
+        self.profile = "search_kernel_rb4096.md"
+
+    def golden(self):
+        path = os.path.join(GOLDEN, "rb4096_oracle.txt")
+        if not os.path.exists(path):
+            return None
+        rows = {}
+        for ln in open(path):
+            if ln.strip() and not ln.startswith("#"):
+                i, n, d, status, nodes = map(int, ln.split())
+                rows[i] = (status, nodes)
+        return rows
+
+    def bytes_per_node(self):
+        """2 n W 4 + 4 (|D(x)| + 2) per table direction woken, from the oracle's event-driven
+        fixpoint on the first 32 instances (first-solution searches, 20 000 nodes at most)."""
+        from oracle import oracle as O
+        nodes, by = 0, 0.0
+        for m in self.models[:32]:
+            r = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1, W=1, node_limit=20000)
+            nodes += r.nodes
+            by += r.work_bytes + r.nodes * 2 * m.n * 4
+        return by / max(nodes, 1)
+
+    def setup(self, K, stream):
+        from paper_1909_09213_gb300 import tune
+        self.tiling, self.tune_entry = tune.tune_batch(self.models, K.CSP_FIRST, calib=512)
+        self.probs = [K.Csp(m) for m in self.models]
+        self.b = K.Batch(self.probs)
+        self.b.stream = stream
+        self.b.set_tiling(self.tiling)
+        self.b.bind(K.CSP_FIRST, stream)
+        self.rc, self.res = self.b.solve(K.CSP_FIRST, use_graph=True, bind=False)
+
+    def launch(self, K):
+        K._check(K.lib().csp_batch_launch(self.b.b, None, 1), "csp_batch_launch")
+
+    def collect(self, K):
+        import ctypes as C
+        import numpy as np
+        res = (K.csp_result * self.count)()
+        words = K.lib().csp_batch_solution_words(self.b.b)
+        self.sol = np.zeros(max(words, 1), dtype=np.int32)
+        rc = K.lib().csp_batch_collect(self.b.b, res, self.sol.ctypes.data_as(K._I32P))
+        if rc != 0:
+            raise RuntimeError(f"batch failed: {rc}")
+        self.res = [{f: getattr(r, f) for f, _ in K.csp_result._fields_} for r in res]
+        st = self.b.stats()
+        st["solutions"] = sum(r["status"] == 1 for r in self.res)
+        st["nodes"] = sum(r["nodes"] for r in self.res)
+        return st
+
+    def e2e_step(self, K):
+        rc, res = self.b.solve(K.CSP_FIRST, use_graph=True, bind=False)
+        st = self.b.stats()
+        st["nodes"] = sum(r["nodes"] for r in res)
+        st["h2d_bytes"] = 0
+        st["d2h_bytes"] = self.count * 40 + 4 * K.lib().csp_batch_solution_words(self.b.b)
+        return st
+
+    def parity(self, st):
+        from oracle import oracle as O
+        g = self.golden()
+        if g is None:
+            return None
+        ok = True
+        for i, (m, r) in enumerate(zip(self.models, self.res)):
+            status, _ = g[i]
+            if status >= 0 and r["status"] != status:
+                ok = False
+            if r["status"] == 1:
+                s = self.sol[r["sol_offset"]:r["sol_offset"] + r["n"]]
+                ok &= O.check_solution(O.OracleModel(m), s)
+        return ok
+
+    def extra(self, K, st):
+        sat = sum(r["status"] == 1 for r in self.res)
+        out = {"instances": self.count, "sat": sat, "unsat": self.count - sat,
+               "time_to_all_first_solutions_ms": st["ms"],
+               "tiling": {f: getattr(self.tiling, f) for f, _ in K.csp_tiling._fields_},
+               "tuned_on": self.tune_entry.get("calib")}
+        # plain first-fail GPU search: the same instances one csp_solve at a time
+        t0 = time.perf_counter()
+        plain_nodes = 0
+        for p in self.probs:
+            rc, ps, _ = p.solve(K.CSP_FIRST)
+            plain_nodes += ps["nodes"]
+        out["plain_first_fail_gpu_ms"] = 1e3 * (time.perf_counter() - t0)
+        out["plain_first_fail_gpu_nodes"] = plain_nodes
+        return out
+
+    def _oracle_instances(self, start, budget_s):
+        from oracle import oracle as O
+        nodes, secs, k = 0, 0.0, start
+        while secs < budget_s and k < self.count:
+            t = time.perf_counter()
+            r = O.solve(O.OracleModel(self.models[k]), mode=1, cap=1, variant=1)
+            secs += time.perf_counter() - t
+            nodes += r.nodes
+            k += 1
+        return nodes, secs, f"model-RB instances {start}..{k - 1} of the batch, first solution each"
+
+    def cpu_sample(self):
+        return self._oracle_instances(0, 12.0)
+
+    def reference_step(self):
+        return self._oracle_instances(0, 1.5)
+
+
 def make_workload(name):
-    from paper_1909_09213_gb300 import instances as I
     if name == "queens16":
-        return "16-queens, all solutions (16 vars, 360 int_ne, 1 uint32 word per domain)", I.queens(16)
+        return Queens(16)
     if name == "queens14":
-        return "14-queens, all solutions (14 vars, 273 int_ne, 1 uint32 word per domain)", I.queens(14)
+        return Queens(14)
+    if name == "rb4096":
+        return RBBatch(4096)
     raise SystemExit(f"unknown workload {name}")
-
-
-def oracle_sample(N, depth=2):
-    """A bounded sample of the N-queens search: the subtree under x0 = 0, x1 = 2 (or x0 = 0
-    with depth 1), solved by the oracle; returns (nodes, seconds, description)."""
-    from oracle import oracle as O
-    from paper_1909_09213_gb300 import instances as I
-    m = I.queens(N)
-    fixed = [(0, 0), (1, 2), (2, 4)][:depth]
-    for (v, a) in fixed:
-        m.removed += [(v, u) for u in range(N) if u != a]
-    om = O.OracleModel(m)
-    t = time.perf_counter()
-    r = O.solve(om, variant=1, W=1)
-    dt = time.perf_counter() - t
-    desc = f"{N}-queens subtree " + ", ".join(f"x{v}={a}" for v, a in fixed)
-    return r.nodes, dt, desc
 
 
 # ----------------------------------------------------------------------------- arms
@@ -166,14 +328,12 @@ def run_reference(args, rank, world):
     """The oracle as it stands, timed on this host, on the same metric and workload."""
     if rank != 0:
         return
-    N = 16 if args.workload == "queens16" else 14
-    desc, _ = make_workload(args.workload)
+    wl = make_workload(args.workload)
     for _ in range(args.warmup):
-        oracle_sample(N, depth=3)
-    nodes, secs = 0, 0.0
-    sample = ""
+        wl.reference_step()
+    nodes, secs, sample = 0, 0.0, ""
     for _ in range(args.steps):
-        n, dt, sample = oracle_sample(N, depth=3)
+        n, dt, sample = wl.reference_step()
         nodes += n
         secs += dt
     value = nodes / secs
@@ -181,7 +341,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": desc, "sample": sample},
+            "config": {"workload": wl.desc, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": 1, "kind": "oracle",
                              "sample": f"{sample}, {nodes // args.steps} nodes per step"},
             "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0,
@@ -197,13 +357,9 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    desc, model = make_workload(args.workload)
-    N = model.n
+    wl = make_workload(args.workload)
     stream = torch.cuda.Stream()
-    p = K.Csp(model)
-    p.stream = stream
-    p.bind(K.CSP_ALL, 0, stream)
-    p.upload(K.CSP_ALL, 0)
+    wl.setup(K, stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB of L2
 
     def step():
@@ -212,12 +368,9 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            p.launch()
+            wl.launch(K)
             e1.record(stream)
-        rc = p.collect()
-        if rc != 0:
-            raise RuntimeError(f"search failed: {rc}")
-        st = p.stats()
+        st = wl.collect(K)
         return e0.elapsed_time(e1), st
 
     for _ in range(args.warmup):
@@ -247,14 +400,15 @@ def run_ours(args, rank, world, local_rank):
         total_ms_max, nodes_all = total_ms, float(nodes)
     value = nodes_all / (total_ms_max * 1e-3)
 
-    # end to end through csp_solve: encode + pinned host-to-device copy + search + read-back
+    # end to end through the public API: host-to-device copies, search, read-back
     e2e_nodes, e2e_secs = 0, 0.0
+    est = None
     for _ in range(max(3, args.steps // 2)):
         with torch.cuda.stream(stream):
             flush.fill_(1)
         stream.synchronize()
         t0 = time.perf_counter()
-        rc, est, _ = p.solve(K.CSP_ALL, 0)
+        est = wl.e2e_step(K)
         e2e_secs += time.perf_counter() - t0
         e2e_nodes += est["nodes"]
     e2e = {"value": e2e_nodes / e2e_secs, "unit": "nodes/s",
@@ -262,38 +416,34 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    golden = golden_row(N)
-    parity = None
-    if golden is not None:
-        parity = (st["nodes"], st["fails"], st["solutions"], st["sol_hash_sum"], st["sol_hash_xor"]) == (
-            golden["nodes"], golden["fails"], golden["solutions"], golden["hash_sum"], golden["hash_xor"])
+    parity = wl.parity(st)
+    extra = wl.extra(K, st)
     smem_peak = K.probe_smem_bandwidth(stream)
-    bpn = bytes_per_node(N)
+    bpn = wl.bytes_per_node()
     kernel_ms = sum(kms) / len(kms)
     roof = None
     if bpn is not None:
         achieved = bpn * st["nodes"] / (kernel_ms * 1e-3) / 1e9
         roof = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                "frac": achieved / smem_peak, "traffic": traffic_from_profile(),
-                "peak_source": "measured: csp_probe_smem_bandwidth (128-bit ld.shared, all SMs)",
-                "bytes_per_node": bpn, "kernel": "search_kernel<1>", "kernel_ms": kernel_ms}
+                "frac": achieved / smem_peak, "traffic": traffic_from_profile(wl.profile),
+                "peak_source": "measured: csp_probe_smem_bandwidth (volatile 128-bit ld.shared, all SMs)",
+                "bytes_per_node": bpn, "kernel": "search_kernel<1, true>", "kernel_ms": kernel_ms}
     cpu = None
     if not args.no_cpu_baseline:
-        n_s, dt, sample = oracle_sample(N, depth=2)
+        n_s, dt, sample = wl.cpu_sample()
         cpu = {"value": n_s / dt, "unit": "nodes/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample} ({n_s} nodes, {dt:.1f} s on one host core)"}
+    config = {"workload": wl.desc, "nodes_per_step": st["nodes"],
+              "l2": "flushed before every step (256 MiB write, untimed)",
+              "workers": st["workers"], "blocks": st["blocks"],
+              "idle_fraction": st["wait_ns"] / max(1.0, st["workers"] * kernel_ms * 1e6),
+              "parity_with_oracle_reference": parity}
+    config.update(extra)
     line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic",
-            "config": {"workload": desc, "nodes_per_step": st["nodes"],
-                       "solutions_per_step": st["solutions"],
-                       "time_to_all_solutions_ms": total_ms_max / args.steps,
-                       "l2": "flushed before every step (256 MiB write, untimed)",
-                       "workers": st["workers"], "blocks": st["blocks"],
-                       "parity_with_oracle_reference": parity},
-            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * args.steps,
-            "roofline": roof, "cpu_baseline": cpu}
+            "data": "synthetic", "config": config, "clocks": clk.summary(), "e2e": e2e,
+            "gpu_launches": 2 * args.steps, "roofline": roof, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -303,7 +453,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="queens16", choices=["queens16", "queens14"])
+    ap.add_argument("--workload", default="queens16", choices=["queens16", "queens14", "rb4096"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -753,6 +753,8 @@ cudaError_t enqueue_batch(csp_batch *b, const SearchArgs &A) {
     cudaError_t e = cudaMemsetAsync(b->ws + b->o_g, 0, sizeof(GState), b->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(b->ws + b->o_teams, 0, (size_t)b->shape.blocks * sizeof(Team), b->stream);
+    if (e == cudaSuccess)   // per-instance counters are accumulated atomically by every helper
+        e = cudaMemsetAsync(b->ws + b->o_res, 0, b->hs.size() * sizeof(InstResult), b->stream);
     if (e == cudaSuccess) e = launch_init_batch(A, b->shape.blocks, b->stream);
     if (e == cudaSuccess)
         e = launch_search(b->W, b->shape.stage_words > 0, A, b->shape.blocks, b->shape.warps * 32,

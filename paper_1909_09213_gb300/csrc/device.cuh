@@ -411,16 +411,92 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
             const int tab = (int)I.w(H_OFF_TAB);
             for (int base = 0; base < n_tab; base += 32) {
                 const int t = base + lane;
-                bool s = false;
-                if (t < n_tab) s = ev_has(evs, (int)I.w(tab + 4 * t)) || ev_has(evs, (int)I.w(tab + 4 * t + 1));
-                uint32_t sm = __ballot_sync(FULLMASK, s);
-                while (sm) {
-                    const int tt = base + __ffs(sm) - 1;
-                    sm &= sm - 1;
-                    if (lane == 0) evals++;
-                    if (revise_table<W, ST>(I, dom, chg, tt)) return true;
+                bool ex = false, ey = false;
+                int x = 0, y = 0;
+                if (t < n_tab) {
+                    x = (int)I.w(tab + 4 * t);
+                    y = (int)I.w(tab + 4 * t + 1);
+                    ex = ev_has(evs, x);
+                    ey = ev_has(evs, y);
+                }
+                if (W == 1) {
+                    // Lanes over the 32 values.  The supported values of x are the union of the
+                    // columns C[b] over b in D(y), those of y the union of the rows R[a] over
+                    // a in D(x): one coalesced load and one OR-reduction per side.  D(x) is
+                    // revised when D(y) changed, D(y) when D(x) changed or was just revised.
+                    // TG scheduled tables go through together as independent chains.
+                    constexpr int TG = 4;
+                    const uint32_t flags = (ex ? 1u : 0u) | (ey ? 2u : 0u);
+                    uint32_t sm = __ballot_sync(FULLMASK, flags != 0u);
+                    if (lane == 0) evals += __popc(sm);
+                    while (sm) {
+                        int tx[TG], ty[TG], Rm[TG], Cm[TG];
+                        uint32_t fl[TG], dx[TG], dy[TG], c[TG];
+#pragma unroll
+                        for (int g = 0; g < TG; ++g) {
+                            const int src = sm ? __ffs(sm) - 1 : 0;
+                            fl[g] = sm ? __shfl_sync(FULLMASK, flags, src) : 0u;
+                            sm &= sm - 1;
+                            tx[g] = __shfl_sync(FULLMASK, x, src);
+                            ty[g] = __shfl_sync(FULLMASK, y, src);
+                            const int e = tab + 4 * (base + src);
+                            Rm[g] = (int)I.w(e + 2);
+                            Cm[g] = (int)I.w(e + 3);
+                        }
+                        // x sides (tables whose y changed)
+#pragma unroll
+                        for (int g = 0; g < TG; ++g) {
+                            dx[g] = SM[dom + tx[g]];
+                            dy[g] = SM[dom + ty[g]];
+                            c[g] = ((fl[g] & 2u) && ((dy[g] >> lane) & 1u)) ? I.w(Cm[g] + lane) : 0u;
+                        }
+#pragma unroll
+                        for (int g = 0; g < TG; ++g) c[g] = __reduce_or_sync(FULLMASK, c[g]);
+#pragma unroll
+                        for (int g = 0; g < TG; ++g) {
+                            if (fl[g] & 2u) {
+                                const uint32_t kx = dx[g] & c[g];
+                                if (kx != dx[g]) {
+                                    if (lane == g) {
+                                        const uint32_t old = atomicAnd(&SM[dom + tx[g]], kx);
+                                        if (old & ~kx) mark_changed(chg, tx[g]);
+                                        if ((old & kx) == 0u) fail = true;
+                                    }
+                                    fl[g] |= 1u;          // D(x) shrank: revise D(y) too
+                                    dx[g] = kx;
+                                }
+                            }
+                        }
+                        // y sides (tables whose x changed or was just revised)
+#pragma unroll
+                        for (int g = 0; g < TG; ++g)
+                            c[g] = ((fl[g] & 1u) && ((dx[g] >> lane) & 1u)) ? I.w(Rm[g] + lane) : 0u;
+#pragma unroll
+                        for (int g = 0; g < TG; ++g) c[g] = __reduce_or_sync(FULLMASK, c[g]);
+#pragma unroll
+                        for (int g = 0; g < TG; ++g) {
+                            if (fl[g] & 1u) {
+                                const uint32_t ky = dy[g] & c[g];
+                                if (ky != dy[g] && lane == g) {
+                                    const uint32_t old = atomicAnd(&SM[dom + ty[g]], ky);
+                                    if (old & ~ky) mark_changed(chg, ty[g]);
+                                    if ((old & ky) == 0u) fail = true;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                } else {
+                    uint32_t sm = __ballot_sync(FULLMASK, ex || ey);
+                    while (sm) {
+                        const int tt = base + __ffs(sm) - 1;
+                        sm &= sm - 1;
+                        if (lane == 0) evals++;
+                        if (revise_table<W, ST>(I, dom, chg, tt)) return true;
+                    }
                 }
             }
+            if (__any_sync(FULLMASK, fail)) return true;
         }
         // 5. linear rows and 6. alldifferent groups whose scope changed
         if (n_lin) {

@@ -110,6 +110,8 @@ struct Worker {
     int top, base;        // open levels [0, top); levels >= base are in shared memory
     uint32_t tick;        // nodes of this worker (low bits pace the periodic checks)
     int gw;               // global worker index
+    int team;             // batch: index of the team (its queue) being helped
+    int inst;             // batch: instance being searched
     int stop;             // a poll saw the stop flag
 
     __device__ __forceinline__ WarpShared &ws() const {
@@ -118,10 +120,10 @@ struct Worker {
     __device__ __forceinline__ int chg() const { return wso; }
     __device__ __forceinline__ int evs() const { return wso + 32; }
     __device__ __forceinline__ uint32_t *qseq() const {
-        return SA.qseq + (SA.batch ? (size_t)blockIdx.x * (SA.qmask + 1) : 0);
+        return SA.qseq + (SA.batch ? (size_t)team * (SA.qmask + 1) : 0);
     }
     __device__ __forceinline__ uint32_t *qrec() const {
-        return SA.qrec + (SA.batch ? (size_t)blockIdx.x * (SA.qmask + 1) * SA.rmax : 0);
+        return SA.qrec + (SA.batch ? (size_t)team * (SA.qmask + 1) * SA.rmax : 0);
     }
     __device__ __forceinline__ uint32_t *spill(int k) const {
         return SA.spill + ((size_t)gw * SA.depth + k) * SA.rmax;
@@ -195,6 +197,7 @@ struct Worker {
             w.sols++;
             w.hsum += h;
             w.hxor ^= h;
+            if (SA.batch) atomicAdd(&SA.results[inst].solutions, 1ull);
         }
         long long slot_off = -1;
         if (SA.mode == 1) {
@@ -442,8 +445,7 @@ template <int W, bool ST>
 #endif
 __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const SearchArgs Ap) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
-    __shared__ int s_inst;
-    __shared__ unsigned long long s_nodes, s_fails, s_sols;
+    __shared__ int s_inst, s_team;
     if (threadIdx.x == 0) SA = Ap;
     __syncthreads();
     const int per_warp = SA.lsm * SA.rmax + WS_WORDS;
@@ -455,6 +457,8 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
     wk.gw = blockIdx.x * SA.warps + warp;
     wk.tick = 0;
     wk.stop = 0;
+    wk.team = 0;
+    wk.inst = 0;
     wk.init_shared();
 
     if (!SA.batch) {
@@ -470,37 +474,60 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
         return;
     }
 
-    Team *T = SA.teams + blockIdx.x;
-    wk.T = T;
+    // Batch mode.  A block takes instance tickets and is the team of each instance it owns;
+    // once the tickets are gone it joins teams whose instance is still being searched
+    // (stages that instance and takes records from the team's queue), so the last, hardest
+    // instances are shared by every block.
     for (;;) {
         if (threadIdx.x == 0) {
-            s_inst = ld_volatile(&SA.g->abort) ? SA.n_inst : atomicAdd(&SA.g->ticket, 1);
-            s_nodes = 0;
-            s_fails = 0;
-            s_sols = 0;
+            const bool aborted = ld_volatile(&SA.g->abort) != 0;
+            int t = aborted ? SA.n_inst : atomicAdd(&SA.g->ticket, 1);
+            int team = blockIdx.x;
+            if (t >= SA.n_inst) {
+                t = -1;
+                team = -1;
+                for (int k = 1; !aborted && k <= (int)gridDim.x; ++k) {
+                    const int c = (blockIdx.x + k) % gridDim.x;
+                    Team *Tc = SA.teams + c;
+                    if (ld_volatile(&Tc->work) > 0) {
+                        __threadfence();
+                        t = ld_volatile(&Tc->inst);
+                        team = c;
+                        break;
+                    }
+                }
+            }
+            s_inst = t;
+            s_team = team;
         }
         __syncthreads();
-        const int i = s_inst;
-        if (i >= SA.n_inst) break;
+        const int i = s_inst, team = s_team;
+        if (i < 0 || i >= SA.n_inst) break;
+        const bool own = team == (int)blockIdx.x;
+        Team *T = SA.teams + team;
         const uint32_t *ib = SA.arena + SA.inst_off[i];
         if (ST) stage_instance(ib);
         __syncthreads();
         wk.I.load(ib);
         wk.S = wk.I.S;
         wk.R = record_words(wk.S, W);
-        const unsigned long long n0 = wk.ws().nodes, f0 = wk.ws().fails, s0 = wk.ws().sols;
+        wk.T = T;
+        wk.team = team;
+        wk.inst = i;
+        const unsigned long long n0 = wk.ws().nodes, f0 = wk.ws().fails;
         if (lane == 0) wk.ws().sol_off = SA.sol_off ? SA.sol_off[i] : 0;
         __syncwarp();
-        if (warp == 0) {
-            if (lane == 0) {
-                T->found = 0;
-                T->work = 1;
-                T->inst = i;
-            }
+        if (own && warp == 0) {
             // root record: the instance's root domains, nothing to try yet, var = -1
             const uint32_t *root = ib + ib[H_OFF_ROOT];
             for (int k = lane; k < wk.R; k += 32)
                 SM[wk.slots + k] = k < wk.S ? root[k] : (k == wk.S + W ? 0xffffffffu : 0u);
+            if (lane == 0) {
+                T->inst = i;
+                T->found = 0;
+                __threadfence();
+                atomicExch(&T->work, 1);
+            }
             __syncwarp();
             __threadfence();
             q_push(T, wk.qseq(), wk.qrec(), wk.slots, nullptr, wk.R, wk.S, W, false, 0u);
@@ -508,19 +535,18 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
         __syncthreads();
         wk.run();
         if (lane == 0) {
-            atomicAdd(&s_nodes, wk.ws().nodes - n0);
-            atomicAdd(&s_fails, wk.ws().fails - f0);
-            atomicAdd(&s_sols, wk.ws().sols - s0);
+            atomicAdd(&SA.results[i].nodes, wk.ws().nodes - n0);
+            atomicAdd(&SA.results[i].fails, wk.ws().fails - f0);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (own && threadIdx.x == 0) {
+            // every record of the instance is finished (work == 0): its verdict is final
             InstResult &r = SA.results[i];
             const int st = ld_volatile(&SA.g->status);
-            r.status = T->found || s_sols > 0 ? 1 : (st != 0 ? st : 0);
+            __threadfence();
+            const unsigned long long sols = *(volatile unsigned long long *)&r.solutions;
+            r.status = ld_volatile(&T->found) || sols > 0 ? 1 : (st != 0 ? st : 0);
             r.n = (int)ib[H_N];
-            r.nodes = s_nodes;
-            r.fails = s_fails;
-            r.solutions = s_sols;
             r.sol_offset = SA.sol_off ? SA.sol_off[i] : 0;
         }
         __syncthreads();
