@@ -202,6 +202,31 @@ int64_t csp_batch_solution_words(const csp_batch_t *b);
 int csp_batch_stats(const csp_batch_t *b, csp_stats_t *out);
 void csp_batch_destroy(csp_batch_t *b);
 
+/* ---------------------------------------------------------------- learned brancher network */
+
+/* The network that scores branching variables: 16 features -> 64 -> 64 -> 1, ReLU, bfloat16
+ * weights and activations, fp32 accumulation (no counterpart in the paper; it only reorders
+ * the search).  Flat parameters (CSP_MLP_PARAMS values): W1 [16][64] row-major, b1[64],
+ * W2 [64][64], b2[64], w3[64], b3[1].  All pointers below are device pointers; every call is
+ * asynchronous on cuda_stream. */
+#define CSP_MLP_PARAMS 5313
+#define CSP_MLP_PACKED_WORDS 2948
+
+/* Fragment-ordered copy of the bf16 parameters (packed_dev: CSP_MLP_PACKED_WORDS uint32). */
+int csp_mlp_pack(const uint16_t *params_dev, uint32_t *packed_dev, void *cuda_stream);
+/* scores_dev[r] for the rows x16 features of X_dev (fp32, rounded to bf16 on load), computed
+ * with warp-level tensor-core tiles of 16 rows. */
+int csp_mlp_forward(const uint32_t *packed_dev, const float *X_dev, int32_t rows, float *scores_dev,
+                    void *cuda_stream);
+/* Mean squared error of the scores against y and its gradient (grad_dev: CSP_MLP_PARAMS fp32;
+ * loss_dev: 1 fp32 or NULL) for fp32 master weights that are rounded to bf16 as in inference. */
+int csp_mlp_grad(const float *master_dev, const float *X_dev, const float *y_dev, int32_t rows,
+                 float *grad_dev, float *loss_dev, void *cuda_stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8; step counts from 1) on master_dev with moments
+ * m_dev, v_dev; params_dev (may be NULL) receives the new bf16 weights. */
+int csp_mlp_adam(float *master_dev, float *m_dev, float *v_dev, const float *grad_dev, int32_t step,
+                 float lr, uint16_t *params_dev, void *cuda_stream);
+
 /* ---------------------------------------------------------------- allocation-free search */
 
 /* csp_solve for callers that cannot allocate device memory: code that runs where

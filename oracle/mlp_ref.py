@@ -59,22 +59,28 @@ def init_params(seed: int = 0) -> np.ndarray:
     return flatten(p).astype(np.float32)
 
 
-def forward(flat, X):
-    """Scores of the rows of X (B x 16): returns s (B,) and the activations."""
+def _act(a, act_round):
+    return bf16_round(a.astype(np.float32)).astype(np.float64) if act_round else a
+
+
+def forward(flat, X, act_round=False):
+    """Scores of the rows of X (B x 16): returns s (B,) and the activations.  With
+    act_round the hidden activations are rounded to bfloat16, as the device stores them."""
     p = unflatten(flat)
     X = np.asarray(X, dtype=np.float64)
     Z1 = X @ p["W1"] + p["b1"]
-    H1 = np.maximum(Z1, 0.0)
+    H1 = _act(np.maximum(Z1, 0.0), act_round)
     Z2 = H1 @ p["W2"] + p["b2"]
-    H2 = np.maximum(Z2, 0.0)
+    H2 = _act(np.maximum(Z2, 0.0), act_round)
     s = H2 @ p["w3"] + p["b3"][0]
     return s, (X, Z1, H1, Z2, H2)
 
 
-def loss_and_grad(flat, X, y):
-    """Mean squared error and its gradient with respect to the flat parameters."""
+def loss_and_grad(flat, X, y, act_round=False):
+    """Mean squared error and its gradient with respect to the flat parameters (the
+    activation rounding, when on, is treated as the identity in the backward pass)."""
     p = unflatten(flat)
-    s, (X, Z1, H1, Z2, H2) = forward(flat, X)
+    s, (X, Z1, H1, Z2, H2) = forward(flat, X, act_round)
     B = X.shape[0]
     r = s - np.asarray(y, dtype=np.float64)
     loss = float(np.mean(r * r))

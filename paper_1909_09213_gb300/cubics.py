@@ -86,6 +86,10 @@ SIGNATURES = {
     "csp_batch_destroy": (None, [_VP]),
     "csp_probe_smem_bandwidth": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_double)]),
     "csp_solve_noalloc": (C.c_int, [_VP, C.c_int32, C.c_int64, _I32P, C.POINTER(csp_limits), _VP]),
+    "csp_mlp_pack": (C.c_int, [_VP, _VP, _VP]),
+    "csp_mlp_forward": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP]),
+    "csp_mlp_grad": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, _VP, _VP]),
+    "csp_mlp_adam": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, C.c_float, _VP, _VP]),
 }
 
 _lib = None
@@ -270,6 +274,47 @@ def probe_smem_bandwidth(stream=None, reps: int = 10) -> float:
     _check(lib().csp_probe_smem_bandwidth(C.c_void_p(out.data_ptr()), _stream_handle(stream),
                                           reps, C.byref(g)), "csp_probe_smem_bandwidth")
     return g.value
+
+
+MLP_PARAMS, MLP_PACKED_WORDS = 5313, 2948
+
+
+def _dp(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def mlp_pack(params_bf16, stream=None):
+    """csp_mlp_pack: uint16 CUDA tensor of MLP_PARAMS -> int32 tensor of packed words."""
+    import torch
+    out = torch.empty(MLP_PACKED_WORDS, dtype=torch.int32, device=params_bf16.device)
+    _check(lib().csp_mlp_pack(_dp(params_bf16), _dp(out), _stream_handle(stream)), "csp_mlp_pack")
+    return out
+
+
+def mlp_forward(packed, X, stream=None):
+    """csp_mlp_forward: scores (float32 CUDA tensor) of the rows of X (rows x 16 float32)."""
+    import torch
+    rows = X.shape[0]
+    out = torch.empty(rows, dtype=torch.float32, device=X.device)
+    _check(lib().csp_mlp_forward(_dp(packed), _dp(X), rows, _dp(out), _stream_handle(stream)),
+           "csp_mlp_forward")
+    return out
+
+
+def mlp_grad(master, X, y, stream=None):
+    """csp_mlp_grad: (gradient tensor, loss tensor) of the mean squared error."""
+    import torch
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(lib().csp_mlp_grad(_dp(master), _dp(X), _dp(y), X.shape[0], _dp(g), _dp(loss),
+                              _stream_handle(stream)), "csp_mlp_grad")
+    return g, loss
+
+
+def mlp_adam(master, m, v, grad, step, lr, params_bf16=None, stream=None):
+    """csp_mlp_adam: in-place Adam step on master (and m, v); refreshes params_bf16."""
+    _check(lib().csp_mlp_adam(_dp(master), _dp(m), _dp(v), _dp(grad), step, lr, _dp(params_bf16),
+                              _stream_handle(stream)), "csp_mlp_adam")
 
 
 class Batch:
