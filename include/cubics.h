@@ -199,6 +199,17 @@ int csp_batch_solve(csp_batch_t *b, int32_t mode, const csp_limits *lim, int32_t
 int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph);
 int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol);
 int64_t csp_batch_solution_words(const csp_batch_t *b);
+/* Brancher of every instance of the batch (as csp_set_brancher). */
+int csp_batch_set_brancher(csp_batch_t *b, int32_t kind, const uint16_t *bf16_weights);
+/* Subtree logging for training the learned brancher (no counterpart in the paper): while
+ * searching, every completed search level whose hash (worker, node count) is 0 mod `sample`
+ * appends 17 floats to log_dev — the 16 features of the level's branching variable when it
+ * was chosen, then log2 of the number of nodes in the level's subtree — at the index returned
+ * by an atomic increment of *count_dev (caller zeroes it), up to cap entries.  Logging keeps
+ * every subtree with the worker that opened it (no donation, no helping blocks), so use one
+ * warp per block.  cap = 0 turns logging off.  log_dev, count_dev: device pointers. */
+int csp_batch_set_log(csp_batch_t *b, float *log_dev, unsigned long long *count_dev, int64_t cap,
+                      uint32_t sample);
 int csp_batch_stats(const csp_batch_t *b, csp_stats_t *out);
 void csp_batch_destroy(csp_batch_t *b);
 

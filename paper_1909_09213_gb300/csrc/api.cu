@@ -22,6 +22,7 @@ cudaError_t launch_init_batch(const SearchArgs &A, int teams, cudaStream_t st);
 cudaError_t launch_propagate(int W, bool staged, const PropArgs &P, int blocks, int threads,
                              size_t smem, cudaStream_t st);
 cudaError_t probe_smem(void *out, cudaStream_t st, int sms, int reps, double *gbs);
+cudaError_t mlp_pack(const uint16_t *params, uint32_t *packed, cudaStream_t st);
 }  // namespace cubics
 
 using namespace cubics;
@@ -61,24 +62,32 @@ DeviceInfo device_info() {
 
 struct Shape {
     int blocks = 0, warps = 0, lsm = 0, qcap = 0, stage_words = 0;
+    int mlp_words = 0;     // staged brancher weights (learned ordering)
+    int feat_words = 0;    // per-warp feature tile (learned ordering)
+    int warp_base = 0;     // shared-memory word where warp 0's area starts
     size_t smem = 0;
 };
 
 // Resources of one search launch.  R and depth are record words and stack levels per
-// worker, cons the words of constraint data to stage in shared memory.
-int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batch, Shape *s) {
+// worker, cons the words of constraint data to stage in shared memory, nmax the largest
+// number of variables (feature tile rows when `learned`).
+int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batch, bool learned,
+               int nmax, Shape *s) {
     s->warps = t.warps_per_block > 0 ? t.warps_per_block : 8;
     if (s->warps > 32) return CSP_EINVAL;
+    s->mlp_words = learned ? CSP_MLP_PACKED_WORDS : 0;
+    s->feat_words = learned ? ((nmax + 15) & ~15) * 8 : 0;
     int lsm = t.smem_levels > 0 ? t.smem_levels : std::max(2, 6144 / R);
     lsm = std::max(2, std::min(lsm, depth));
     const int cons4 = (cons + 3) & ~3;
-    size_t smem = (size_t)s->warps * (lsm * R + WS_WORDS) * 4;
-    while (smem > SMEM_MAX && lsm > 2) {
-        lsm--;
-        smem = (size_t)s->warps * (lsm * R + WS_WORDS) * 4;
-    }
+    auto bytes = [&](int l) {
+        return ((size_t)s->warps * (l * R + WS_WORDS + s->feat_words) + s->mlp_words) * 4;
+    };
+    size_t smem = bytes(lsm);
+    while (smem > SMEM_MAX && lsm > 2) smem = bytes(--lsm);
     if (smem > SMEM_MAX) return CSP_ETOOBIG;
     s->stage_words = (smem + (size_t)cons4 * 4 <= SMEM_MAX) ? cons4 : 0;
+    s->warp_base = s->stage_words + s->mlp_words;
     s->smem = smem + (size_t)s->stage_words * 4;
     s->lsm = lsm;
     int q = t.queue_records > 0 ? t.queue_records : (batch ? 64 : 4096);
@@ -141,8 +150,9 @@ struct csp {
     GState *pin_g = nullptr;         // pinned host copy of the launch counters
     Shape shape;
     size_t o_inst = 0, o_off = 0, o_g = 0, o_team = 0, o_qseq = 0, o_qrec = 0, o_spill = 0,
-           o_sols = 0;
+           o_sols = 0, o_mlp_params = 0, o_mlp_packed = 0;
     int R = 0, depth = 0;
+    std::vector<uint16_t> mlp_params;    // learned brancher weights (bf16)
     csp_stats_t stats{};
 };
 
@@ -253,6 +263,61 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
         B[tab_hdr + 4 * t + 2] = (uint32_t)offR;
         B[tab_hdr + 4 * t + 3] = (uint32_t)offC;
     }
+    // static data for the learned brancher's features, and neighbour lists
+    {
+        std::vector<int> deg(n, 0), kne(n, 0), klin(n, 0), kad(n, 0), ktab(n, 0);
+        std::vector<double> tight(n, 0.0);
+        std::vector<std::vector<int32_t>> nb(n);
+        auto link = [&](int a, int b) {
+            if (a != b) { nb[a].push_back(b); nb[b].push_back(a); }
+        };
+        for (size_t k = 0; k < h->ne_x.size(); ++k) {
+            const int x = h->ne_x[k], y = h->ne_y[k];
+            deg[x]++; kne[x]++;
+            if (y >= 0 && y != x) { deg[y]++; kne[y]++; link(x, y); }
+        }
+        for (const LinRow &r : h->lin) {
+            for (int32_t v : r.var) { deg[v]++; klin[v]++; }
+            for (size_t a = 0; a < r.var.size(); ++a)
+                for (size_t b = a + 1; b < r.var.size(); ++b) link(r.var[a], r.var[b]);
+        }
+        for (const auto &g : h->ad) {
+            for (int32_t v : g) { deg[v]++; kad[v]++; }
+            for (size_t a = 0; a < g.size(); ++a)
+                for (size_t b = a + 1; b < g.size(); ++b) link(g[a], g[b]);
+        }
+        for (const Table &T : h->tab) {
+            size_t allowed = 0;
+            for (uint8_t f : T.allowed) allowed += f;
+            const double forb = 1.0 - (double)allowed / (double)std::max<size_t>(1, T.allowed.size());
+            deg[T.x]++; ktab[T.x]++; tight[T.x] += forb;
+            deg[T.y]++; ktab[T.y]++; tight[T.y] += forb;
+            link(T.x, T.y);
+        }
+        int maxdeg = 1;
+        for (int v = 0; v < n; ++v) maxdeg = std::max(maxdeg, deg[v]);
+        B[H_MAXDEG] = (uint32_t)maxdeg;
+        B[H_OFF_VFEAT] = (uint32_t)B.size();
+        for (int v = 0; v < n; ++v) {
+            const float t = ktab[v] ? (float)(tight[v] / ktab[v]) : 0.f;
+            uint32_t tb;
+            std::memcpy(&tb, &t, 4);
+            put((uint32_t)(h->lo[v] - lo0)); put((uint32_t)(h->hi[v] - h->lo[v] + 1));
+            put((uint32_t)deg[v]); put((uint32_t)kne[v]); put((uint32_t)klin[v]);
+            put((uint32_t)kad[v]); put((uint32_t)ktab[v]); put(tb);
+        }
+        B[H_OFF_NB_START] = (uint32_t)B.size();
+        uint32_t s0 = 0;
+        for (int v = 0; v < n; ++v) {
+            std::sort(nb[v].begin(), nb[v].end());
+            nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
+            put(s0);
+            s0 += (uint32_t)nb[v].size();
+        }
+        put(s0);
+        B[H_OFF_NB] = (uint32_t)B.size();
+        for (int v = 0; v < n; ++v) for (int32_t u : nb[v]) put((uint32_t)u);
+    }
     align4();
     B[H_CONS_WORDS] = (uint32_t)B.size();
     B[H_OFF_ROOT] = (uint32_t)B.size();
@@ -293,8 +358,9 @@ int plan_single(csp *h, int32_t mode, int64_t cap, size_t *bytes, std::vector<ui
     }
     const int R = record_words(h->n * h->W, h->W);
     const int depth = h->n + 1;
+    const bool learned = h->brancher == CSP_BR_LEARNED;
     Shape s;
-    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, &s);
+    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, learned, h->n, &s);
     if (rc) return rc;
     h->shape = s;
     h->R = R;
@@ -305,8 +371,26 @@ int plan_single(csp *h, int32_t mode, int64_t cap, size_t *bytes, std::vector<ui
     h->o_qrec = c.take((size_t)s.qcap * R * 4);
     h->o_spill = c.take((size_t)s.blocks * s.warps * depth * R * 4);
     h->o_sols = c.take((size_t)std::max<int64_t>(cap, 1) * h->n * 4);
+    h->o_mlp_params = c.take(learned ? CSP_MLP_PARAMS * 2 : 0);
+    h->o_mlp_packed = c.take(learned ? CSP_MLP_PACKED_WORDS * 4 : 0);
     *bytes = c.off;
     return CSP_OK;
+}
+
+// the brancher's bf16 parameters into the workspace, then their fragment-ordered copy
+cudaError_t upload_mlp(const std::vector<uint16_t> &params, uint8_t *ws, size_t o_params,
+                       size_t o_packed, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(ws + o_params, params.data(), params.size() * 2,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = mlp_pack((const uint16_t *)(ws + o_params), (uint32_t *)(ws + o_packed), st);
+    return e;
+}
+
+void set_learned_args(SearchArgs &A, const Shape &s, bool learned, const uint8_t *ws, size_t o_packed) {
+    A.mlp = learned ? (const uint32_t *)(ws + o_packed) : nullptr;
+    A.mlp_off = learned ? s.stage_words : -1;
+    A.feat_words = s.feat_words;
+    A.warp_base = s.warp_base;
 }
 
 SearchArgs single_args(csp *h, int32_t mode, int64_t cap, const csp_limits *lim) {
@@ -336,7 +420,12 @@ SearchArgs single_args(csp *h, int32_t mode, int64_t cap, const csp_limits *lim)
     A.node_limit = lim ? lim->node_limit : 0;
     A.deadline_ns = lim ? lim->time_limit_ns : 0;
     A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
-    A.mlp = nullptr;
+    set_learned_args(A, h->shape, h->brancher == CSP_BR_LEARNED, w, h->o_mlp_packed);
+    A.log_extra = 0;
+    A.log_sample = 1;
+    A.logbuf = nullptr;
+    A.log_count = nullptr;
+    A.log_cap = 0;
     A.part = h->part;
     A.nparts = h->nparts;
     return A;
@@ -483,10 +572,13 @@ int csp_set_partition(csp_t *h, int32_t part, int32_t nparts) {
 }
 
 int csp_set_brancher(csp_t *h, int32_t kind, const uint16_t *bf16_weights) {
-    (void)bf16_weights;
-    if (!h) return CSP_EINVAL;
-    if (kind != CSP_BR_FIRST_FAIL) return CSP_EINVAL;
+    if (!h || (kind != CSP_BR_FIRST_FAIL && kind != CSP_BR_LEARNED)) return CSP_EINVAL;
+    if (kind == CSP_BR_LEARNED) {
+        if (bf16_weights) h->mlp_params.assign(bf16_weights, bf16_weights + CSP_MLP_PARAMS);
+        if (h->mlp_params.size() != (size_t)CSP_MLP_PARAMS) return CSP_EINVAL;
+    }
     h->brancher = kind;
+    invalidate(h);
     return CSP_OK;
 }
 
@@ -497,6 +589,7 @@ int csp_workspace_bytes(const csp_t *hc, int32_t mode, int64_t cap, size_t *byte
     tmp.ne_x = hc->ne_x; tmp.ne_y = hc->ne_y; tmp.ne_c = hc->ne_c;
     tmp.lin = hc->lin; tmp.ad = hc->ad; tmp.tab = hc->tab;
     tmp.lo0 = hc->lo0; tmp.W = hc->W; tmp.tiling = hc->tiling;
+    tmp.brancher = hc->brancher; tmp.part = hc->part; tmp.nparts = hc->nparts;
     return plan_single(&tmp, mode, cap, bytes, nullptr);
 }
 
@@ -547,9 +640,12 @@ int csp_upload(csp_t *h, int32_t mode, int64_t cap) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->ws + h->o_off, h->pin_block + h->block.size(), sizeof(int64_t),
                             cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->brancher == CSP_BR_LEARNED)
+        e = upload_mlp(h->mlp_params, h->ws, h->o_mlp_params, h->o_mlp_packed, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    h->stats.h2d_bytes = (int64_t)h->block.size() * 4 + (int64_t)sizeof(int64_t);
+    h->stats.h2d_bytes = (int64_t)h->block.size() * 4 + (int64_t)sizeof(int64_t) +
+                         (h->brancher == CSP_BR_LEARNED ? CSP_MLP_PARAMS * 2 : 0);
     h->uploaded = true;
     h->up_mode = mode;
     h->up_cap = cap;
@@ -685,7 +781,14 @@ struct csp_batch {
     bool uploaded = false;
     int32_t mode = -1;
     size_t o_arena = 0, o_ioff = 0, o_soff = 0, o_g = 0, o_teams = 0, o_qseq = 0, o_qrec = 0,
-           o_spill = 0, o_sols = 0, o_res = 0;
+           o_spill = 0, o_sols = 0, o_res = 0, o_mlp_params = 0, o_mlp_packed = 0;
+    int nmax = 1;
+    int32_t brancher = CSP_BR_FIRST_FAIL;
+    std::vector<uint16_t> mlp_params;
+    float *logbuf = nullptr;                 // subtree logging (caller-owned device buffers)
+    unsigned long long *log_count = nullptr;
+    int64_t log_cap = 0;
+    uint32_t log_sample = 1;
     cudaGraphExec_t graph = nullptr;
     int32_t graph_mode = -1;
     csp_limits graph_lim{};
@@ -696,7 +799,9 @@ namespace {
 
 int plan_batch(csp_batch *b, int32_t mode, size_t *bytes) {
     Shape s;
-    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, &s);
+    const bool learned = b->brancher == CSP_BR_LEARNED;
+    b->R = record_words(b->nmax * b->W, b->W, b->logbuf ? LOG_EXTRA : 0);
+    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, learned, b->nmax, &s);
     if (rc) return rc;
     (void)mode;
     b->shape = s;
@@ -712,6 +817,8 @@ int plan_batch(csp_batch *b, int32_t mode, size_t *bytes) {
     b->o_spill = c.take((size_t)s.blocks * s.warps * b->depth * b->R * 4);
     b->o_sols = c.take((size_t)std::max<int64_t>(b->sol_words, 1) * 4);
     b->o_res = c.take(count * sizeof(InstResult));
+    b->o_mlp_params = c.take(learned ? CSP_MLP_PARAMS * 2 : 0);
+    b->o_mlp_packed = c.take(learned ? CSP_MLP_PACKED_WORDS * 4 : 0);
     *bytes = c.off;
     return CSP_OK;
 }
@@ -743,7 +850,13 @@ SearchArgs batch_args(csp_batch *b, const csp_limits *lim) {
     A.node_limit = lim ? lim->node_limit : 0;
     A.deadline_ns = lim ? lim->time_limit_ns : 0;
     A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
-    A.mlp = nullptr;
+    set_learned_args(A, b->shape, b->brancher == CSP_BR_LEARNED, w, b->o_mlp_packed);
+    A.log_extra = b->logbuf ? LOG_EXTRA : 0;
+    A.log_sample = b->log_sample;
+    A.logbuf = b->logbuf;
+    A.log_count = b->log_count;
+    A.log_cap = b->log_cap;
+    if (b->logbuf) A.flags |= CSP_F_NO_DONATE;      // a level's subtree must stay with one worker
     A.part = 0;
     A.nparts = 1;
     return A;
@@ -785,6 +898,7 @@ int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count) {
     int W = 1, nmax = 1;
     for (csp *h : b->hs) { W = std::max(W, h->W); nmax = std::max(nmax, h->n); }
     b->W = W;
+    b->nmax = nmax;
     b->depth = nmax + 1;
     b->R = record_words(nmax * W, W);
     int64_t sw = 0;
@@ -817,8 +931,33 @@ int csp_batch_workspace_bytes(const csp_batch_t *bc, int32_t mode, size_t *bytes
     csp_batch tmp;
     tmp.hs = bc->hs; tmp.W = bc->W; tmp.R = bc->R; tmp.depth = bc->depth;
     tmp.cons_max = bc->cons_max; tmp.arena = bc->arena; tmp.sol_words = bc->sol_words;
-    tmp.tiling = bc->tiling;
+    tmp.tiling = bc->tiling; tmp.nmax = bc->nmax; tmp.brancher = bc->brancher;
+    tmp.logbuf = bc->logbuf;
     return plan_batch(&tmp, mode, bytes);
+}
+
+int csp_batch_set_brancher(csp_batch_t *b, int32_t kind, const uint16_t *bf16_weights) {
+    if (!b || (kind != CSP_BR_FIRST_FAIL && kind != CSP_BR_LEARNED)) return CSP_EINVAL;
+    if (kind == CSP_BR_LEARNED) {
+        if (bf16_weights) b->mlp_params.assign(bf16_weights, bf16_weights + CSP_MLP_PARAMS);
+        if (b->mlp_params.size() != (size_t)CSP_MLP_PARAMS) return CSP_EINVAL;
+    }
+    b->brancher = kind;
+    b->uploaded = false;
+    drop_graph(b);
+    return CSP_OK;
+}
+
+int csp_batch_set_log(csp_batch_t *b, float *log_dev, unsigned long long *count_dev, int64_t cap,
+                      uint32_t sample) {
+    if (!b || cap < 0 || (cap > 0 && (!log_dev || !count_dev))) return CSP_EINVAL;
+    b->logbuf = cap > 0 ? log_dev : nullptr;
+    b->log_count = cap > 0 ? count_dev : nullptr;
+    b->log_cap = cap;
+    b->log_sample = sample < 1 ? 1 : sample;
+    b->uploaded = false;
+    drop_graph(b);
+    return CSP_OK;
 }
 
 int csp_batch_bind(csp_batch_t *b, void *dev, size_t bytes, void *cuda_stream) {
@@ -850,6 +989,8 @@ static int batch_upload(csp_batch *b, int32_t mode) {
         e = cudaMemcpyAsync(b->ws + b->o_ioff, b->inst_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->ws + b->o_soff, b->sol_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && b->brancher == CSP_BR_LEARNED)
+        e = upload_mlp(b->mlp_params, b->ws, b->o_mlp_params, b->o_mlp_packed, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (b->mode != mode) drop_graph(b);
@@ -1015,6 +1156,8 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->ws + h->o_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->brancher == CSP_BR_LEARNED)
+        e = upload_mlp(h->mlp_params, h->ws, h->o_mlp_params, h->o_mlp_packed, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_g, 0, sizeof(GState), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_team, 0, sizeof(Team), h->stream);
     if (e == cudaSuccess) e = launch_init_single(A, h->stream);

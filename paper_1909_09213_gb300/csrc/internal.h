@@ -25,8 +25,17 @@ enum Hdr {
     H_N_AD, H_OFF_AD_ROW, H_OFF_AD_MEM, H_AD_MW, H_OFF_AD_MASK,
     H_N_TAB, H_OFF_TAB,
     H_OFF_ROOT, H_CONS_WORDS, H_TOTAL, H_R, H_N_NE,
+    H_OFF_VFEAT,                      // per variable VFEAT_WORDS words of static feature data
+    H_OFF_NB_START, H_OFF_NB,         // neighbour lists: n+1 starts; neighbour indices
+    H_MAXDEG,                         // largest constraint degree of a variable
     H_COUNT
 };
+
+// static feature data of a variable: offset of its own lo from lo0, initial domain size,
+// constraint degree, counts of ne / lin / alldiff / table constraints, mean forbidden
+// fraction of its tables (float bits)
+constexpr int VFEAT_WORDS = 8;
+constexpr int N_FEATURES = 16;
 static_assert(H_COUNT <= HDR_WORDS, "header too long");
 
 // lin row: 3 words (first term, number of terms, rhs); term: 2 words (coef, var)
@@ -35,8 +44,13 @@ static_assert(H_COUNT <= HDR_WORDS, "header too long");
 //        words: R row a = values of y compatible with x = lo0 + a, C row b the transpose.
 
 // Search-stack level / work record: R words = S domain words, W words of values still to
-// try, one word with the branching variable (-1: the record is a node to propagate).
-__host__ __device__ inline int record_words(int S, int W) { return (S + W + 1 + 3) & ~3; }
+// try, one word with the branching variable (-1: the record is a node to propagate), and
+// `extra` words (subtree logging: the node count at the level's creation and the chosen
+// variable's 16 features).
+__host__ __device__ inline int record_words(int S, int W, int extra = 0) {
+    return (S + W + 1 + extra + 3) & ~3;
+}
+constexpr int LOG_EXTRA = 1 + 16;
 
 struct Team {                 // one work-sharing group (whole grid or one block)
     int32_t work;             // records queued or being explored
@@ -92,7 +106,15 @@ struct SearchArgs {
     long long node_limit;
     long long deadline_ns;    // time limit from each worker's start, 0 = none
     long long wait_limit_ns;
-    const uint16_t *mlp;      // learned brancher weights (bf16), NULL = first-fail
+    const uint32_t *mlp;      // learned brancher: packed network weights, NULL = first-fail
+    int32_t mlp_off;          // SM word offset of the staged weights, -1 = first-fail
+    int32_t feat_words;       // per-warp words of the learned brancher's feature tile
+    int32_t warp_base;        // SM word offset of warp 0's area
+    int32_t log_extra;        // subtree logging: LOG_EXTRA extra record words, else 0
+    uint32_t log_sample;      // log one completed level in log_sample (hash of worker, count)
+    float *logbuf;            // log entries of 17 floats: 16 features, log2 subtree nodes
+    unsigned long long *log_count;
+    long long log_cap;
 };
 
 struct PropArgs {

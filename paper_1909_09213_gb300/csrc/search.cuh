@@ -17,6 +17,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "device.cuh"
+#include "mlp.cuh"
 
 namespace cubics {
 
@@ -247,6 +248,141 @@ struct Worker {
         }
     }
 
+    // ---------------------------------------------------------------- learned brancher
+
+    // number of fixed variables of the node at C (every lane)
+    __device__ int count_fixed_lane0(int C) const {
+        int c = 0;
+        for (int v = lane_id(); v < I.n; v += 32) c += dom_popc<W>(C + v * W) == 1;
+        return __reduce_add_sync(FULLMASK, c);
+    }
+
+    // mean over the variables of |D| / initial size at the node C (every lane)
+    __device__ float mean_rel_size(int C) const {
+        const int vfo = (int)I.w(H_OFF_VFEAT);
+        float s = 0.f;
+        for (int v = lane_id(); v < I.n; v += 32)
+            s += (float)dom_popc<W>(C + v * W) / (float)I.w(vfo + VFEAT_WORDS * v + 1);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULLMASK, s, o);
+        return s / (float)I.n;
+    }
+
+    // The 16 features of variable v at the node C (one lane): domain size, log size, degree,
+    // unfixed neighbours, neighbours' relative size, bounds, mean relative domain size of the
+    // node, fraction fixed, mix of
+    // constraint kinds, mean table tightness, size per unfixed neighbour, bias.
+    // Every feature depends only on the node's domains and the model, so the learned choice
+    // is the same whichever worker expands the node.
+    __device__ void var_features(int C, int v, float mrel, int nfixed, float (&f)[N_FEATURES]) const {
+        const int vfo = (int)I.w(H_OFF_VFEAT);
+        const int vf = vfo + VFEAT_WORDS * v;
+        const int lo_off = (int)I.w(vf), size0 = (int)I.w(vf + 1), deg = (int)I.w(vf + 2);
+        const int d = C + v * W;
+        const int pc = dom_popc<W>(d), mn = dom_min<W>(d), mx = dom_max<W>(d);
+        const int nbs = (int)I.w(H_OFF_NB_START), nbl = (int)I.w(H_OFF_NB);
+        const int k0 = (int)I.w(nbs + v), k1 = (int)I.w(nbs + v + 1);
+        int unfixed = 0;
+        float rel = 0.f;
+        for (int k = k0; k < k1; ++k) {
+            const int u = (int)I.w(nbl + k);
+            const int pu = dom_popc<W>(C + u * W);
+            if (pu > 1) {
+                unfixed++;
+                rel += (float)pu / (float)I.w(vfo + VFEAT_WORDS * u + 1);
+            }
+        }
+        const float s0 = (float)max(size0, 2), span = (float)max(size0 - 1, 1);
+        const float dg = (float)max(deg, 1);
+        f[0] = (float)pc / s0;
+        f[1] = __log2f((float)max(pc, 1)) / __log2f(s0);
+        f[2] = (float)deg / (float)I.w(H_MAXDEG);
+        f[3] = (float)unfixed / (float)max(k1 - k0, 1);
+        f[4] = unfixed ? rel / (float)unfixed : 0.f;
+        f[5] = (float)(mn - lo_off) / span;
+        f[6] = (float)(mx - lo_off) / span;
+        f[7] = mrel;
+        f[8] = (float)nfixed / (float)I.n;
+        f[9] = (float)I.w(vf + 3) / dg;
+        f[10] = (float)I.w(vf + 4) / dg;
+        f[11] = (float)I.w(vf + 5) / dg;
+        f[12] = (float)I.w(vf + 6) / dg;
+        f[13] = __uint_as_float(I.w(vf + 7));
+        f[14] = (float)pc / (s0 * (float)(1 + unfixed));
+        f[15] = 1.f;
+    }
+
+    // The unfixed variable with the smallest predicted log2 subtree size (ties: fewest
+    // values, then lowest index).  Falls back to the first-fail choice y_ff when a score is
+    // not a number.  Feature rows are staged as bf16 pairs in the warp's tile; the network
+    // runs on the tensor cores, 16 variables per mma tile.
+    __device__ __noinline__ int select_learned(int C, int y_ff) {
+        const int lane = lane_id();
+        const int n = I.n;
+        const int feat = wso + WS_WORDS;
+        const int nfixed = count_fixed_lane0(C);
+        const float mrel = mean_rel_size(C);
+        const int npad = (n + 15) & ~15;
+        for (int v = lane; v < npad; v += 32) {
+            float f[N_FEATURES];
+            if (v < n) var_features(C, v, mrel, nfixed, f);
+#pragma unroll
+            for (int j = 0; j < N_FEATURES / 2; ++j)
+                SM[feat + v * 8 + j] = v < n ? pack_bf16(f[2 * j], f[2 * j + 1]) : 0u;
+        }
+        __syncwarp();
+        unsigned long long best = ~0ull;
+        bool nan = false;
+        const int g = lane >> 2;
+        for (int r0 = 0; r0 < npad; r0 += 16) {
+            auto x = [&](int r, int c) -> uint32_t { return SM[feat + (r0 + r) * 8 + (c >> 1)]; };
+            auto pk = [&](int i) -> uint32_t { return SM[SA.mlp_off + i]; };
+            float s_lo, s_hi;
+            mlp_tile(x, pk, s_lo, s_hi);
+            if ((lane & 3) == 0) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int v = r0 + g + 8 * h;
+                    const float sc = h ? s_hi : s_lo;
+                    if (v < n) {
+                        const int pc = dom_popc<W>(C + v * W);
+                        if (pc > 1) {
+                            if (sc != sc) nan = true;
+                            const uint32_t u = __float_as_uint(sc);
+                            const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+                            const unsigned long long key =
+                                ((unsigned long long)ord << 32) | ((unsigned)pc << 16) | (unsigned)v;
+                            best = key < best ? key : best;
+                        }
+                    }
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(FULLMASK, best, o);
+            best = other < best ? other : best;
+        }
+        if (__any_sync(FULLMASK, nan) || best == ~0ull) return y_ff;
+        return (int)(best & 0xffffu);
+    }
+
+    // subtree logging: the level at P is complete; its subtree had nodes - start nodes
+    __device__ __noinline__ void log_level(int P) {
+        if (lane_id() == 0) {
+            const uint32_t start = SM[P + S + W + 1];
+            const uint32_t size = (uint32_t)ws().nodes - start;
+            const uint32_t h = (uint32_t)splitmix64(((unsigned long long)gw << 32) | start);
+            if (size > 0 && (SA.log_sample <= 1 || h % SA.log_sample == 0)) {
+                const unsigned long long slot = atomicAdd(SA.log_count, 1ull);
+                if ((long long)slot < SA.log_cap) {
+                    float *e = SA.logbuf + slot * (N_FEATURES + 1);
+                    for (int i = 0; i < N_FEATURES; ++i) e[i] = __uint_as_float(SM[P + S + W + 2 + i]);
+                    e[N_FEATURES] = __log2f((float)size);
+                }
+            }
+        }
+        __syncwarp();
+    }
+
     // propagate the node in the shared slot C of level cl; open a level on success
     __device__ void node(int C, int cl, bool full) {
         const int lane = lane_id();
@@ -277,11 +413,25 @@ struct Worker {
             refill();
             return;
         }
-        const int y = select_first_fail<W>(C, I.n);
+        int y = select_first_fail<W>(C, I.n);
         if (y < 0) {
             if (counted) record_solution(C);
             refill();
             return;
+        }
+        if (SA.mlp_off >= 0) y = select_learned(C, y);
+        if (SA.log_extra) {
+            // subtree logging: remember the node count and the chosen variable's features
+            float f[N_FEATURES];
+            const int nfixed = count_fixed_lane0(C);          // warp-wide reductions
+            const float mrel = mean_rel_size(C);
+            if (lane == 0) {
+                var_features(C, y, mrel, nfixed, f);
+                SM[C + S + W + 1] = (uint32_t)ws().nodes;
+#pragma unroll
+                for (int i = 0; i < N_FEATURES; ++i) SM[C + S + W + 2 + i] = __float_as_uint(f[i]);
+            }
+            __syncwarp();
         }
         uint32_t rw = lane < W ? SM[C + y * W + lane] : 0u;
         if (split_root) {
@@ -317,6 +467,7 @@ struct Worker {
         const uint32_t r = lane < W ? SM[P + S + lane] : 0u;
         const uint32_t nz = __ballot_sync(FULLMASK, r != 0u);
         if (!nz) {
+            if (SA.log_extra) log_level(P);
             top = p;
             refill();
             return;
@@ -325,7 +476,9 @@ struct Worker {
         const uint32_t rw = __shfl_sync(FULLMASK, r, k);
         const int v = (k << 5) + __ffs(rw) - 1;
         const uint32_t rest = rw & (rw - 1);
-        const bool last = rest == 0u && (nz & ~(1u << k)) == 0u;
+        // the last value reuses the level's slot, unless the level must outlive its last
+        // child to measure its subtree
+        const bool last = rest == 0u && (nz & ~(1u << k)) == 0u && !SA.log_extra;
         const int x = (int)SM[P + S + W];
         int C, cl;
         __syncwarp();
@@ -448,11 +601,15 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
     __shared__ int s_inst, s_team;
     if (threadIdx.x == 0) SA = Ap;
     __syncthreads();
-    const int per_warp = SA.lsm * SA.rmax + WS_WORDS;
+    const int per_warp = SA.lsm * SA.rmax + WS_WORDS + SA.feat_words;
+    if (SA.mlp_off >= 0) {           // the brancher's weights, staged once per block
+        for (int i = threadIdx.x; i < PK_WORDS; i += blockDim.x) SM[SA.mlp_off + i] = __ldg(SA.mlp + i);
+        __syncthreads();
+    }
 
     Worker<W, ST> wk;
     wk.lsm = SA.lsm;
-    wk.slots = SA.stage_words + warp * per_warp;
+    wk.slots = SA.warp_base + warp * per_warp;
     wk.wso = wk.slots + SA.lsm * SA.rmax;
     wk.gw = blockIdx.x * SA.warps + warp;
     wk.tick = 0;
@@ -467,7 +624,7 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
         __syncthreads();
         wk.I.load(ib);
         wk.S = wk.I.S;
-        wk.R = record_words(wk.S, W);
+        wk.R = record_words(wk.S, W, SA.log_extra);
         wk.T = SA.teams;
         wk.run();
         wk.flush();
@@ -486,7 +643,9 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
             if (t >= SA.n_inst) {
                 t = -1;
                 team = -1;
-                for (int k = 1; !aborted && k <= (int)gridDim.x; ++k) {
+                // helpers can only take donated work: no joining when donation is off
+                const bool join = !aborted && !(SA.flags & F_NO_DONATE);
+                for (int k = 1; join && k <= (int)gridDim.x; ++k) {
                     const int c = (blockIdx.x + k) % gridDim.x;
                     Team *Tc = SA.teams + c;
                     if (ld_volatile(&Tc->work) > 0) {
@@ -510,7 +669,7 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
         __syncthreads();
         wk.I.load(ib);
         wk.S = wk.I.S;
-        wk.R = record_words(wk.S, W);
+        wk.R = record_words(wk.S, W, SA.log_extra);
         wk.T = T;
         wk.team = team;
         wk.inst = i;

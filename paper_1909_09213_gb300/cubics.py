@@ -82,6 +82,8 @@ SIGNATURES = {
     "csp_batch_launch": (C.c_int, [_VP, C.POINTER(csp_limits), C.c_int32]),
     "csp_batch_collect": (C.c_int, [_VP, C.POINTER(csp_result), _I32P]),
     "csp_batch_solution_words": (C.c_int64, [_VP]),
+    "csp_batch_set_brancher": (C.c_int, [_VP, C.c_int32, _U16P]),
+    "csp_batch_set_log": (C.c_int, [_VP, _VP, _VP, C.c_int64, C.c_uint32]),
     "csp_batch_stats": (C.c_int, [_VP, C.POINTER(csp_stats_t)]),
     "csp_batch_destroy": (None, [_VP]),
     "csp_probe_smem_bandwidth": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_double)]),
@@ -250,6 +252,14 @@ class Csp:
         s = csp_stats_t()
         _check(lib().csp_stats(self.h, C.byref(s)), "csp_stats")
         return _stats_dict(s)
+
+    def set_brancher(self, kind: int, params_bf16=None):
+        """csp_set_brancher: first-fail, or learned with bf16 weights (uint16 array)."""
+        p = None
+        if params_bf16 is not None:
+            self._mlp = np.ascontiguousarray(params_bf16, dtype=np.uint16)
+            p = self._mlp.ctypes.data_as(_U16P)
+        _check(lib().csp_set_brancher(self.h, kind, p), "csp_set_brancher")
 
     def propagate(self, dom_in: np.ndarray):
         """csp_propagate on `count` states of n*W words: returns (dom_out, failed)."""
