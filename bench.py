@@ -27,6 +27,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -312,6 +314,87 @@ class RBBatch:
         return self._oracle_instances(0, 1.5)
 
 
+class LearnedRB(RBBatch):
+    """The learning configuration: the network is trained on subtree logs of 20000 exhaustive
+    searches (n = 30, d = 16); a step solves 1024 held-out instances (n = 80, d = 20, first
+    solution) in one launch with the learned brancher.  The same batch under first-fail is
+    timed alongside (time-to-solution at identical verdicts)."""
+
+    def __init__(self, train_count=20000, eval_count=1024):
+        from paper_1909_09213_gb300 import instances as I
+        self.count = eval_count
+        self.train_count = train_count
+        self.models = I.rb_batch(eval_count, n_range=(80, 80), d_range=(20, 20), config_id=I.CFG_RB_EVAL)
+        self.desc = (f"{eval_count} held-out model-RB instances n=80, d=20, first solution, learned "
+                     f"brancher trained on {train_count} exhaustive searches (n=30, d=16)")
+        self.profile = "search_kernel_rb_learned.md"
+
+    def golden(self):
+        return None
+
+    def bytes_per_node(self):
+        """as for the model-RB batch, from the oracle's first-fail searches of 4 held-out
+        instances (the learned order does not change what one node moves)"""
+        from oracle import oracle as O
+        nodes, by = 0, 0.0
+        for m in self.models[:4]:
+            r = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1, W=1, node_limit=20000)
+            nodes += r.nodes
+            by += r.work_bytes + r.nodes * 2 * m.n * 4
+        return by / max(nodes, 1)
+
+    def setup(self, K, stream):
+        from paper_1909_09213_gb300 import instances as I
+        from paper_1909_09213_gb300 import learn
+        t0 = time.time()
+        train_models = I.rb_batch(self.train_count, n_range=(30, 30), d_range=(16, 16),
+                                  config_id=I.CFG_RB_TRAIN)
+        data, self.cinfo = learn.collect(train_models, cap=8_000_000, sample=1)
+        self.params, self.tinfo = learn.train(data, epochs=8)
+        self.prep_s = time.time() - t0
+        self.tiling = K.tiling(warps_per_block=4, smem_levels=8)
+        self.tune_entry = {"calib": None}
+        self.probs = [K.Csp(m) for m in self.models]
+        self.b = K.Batch(self.probs)
+        self.b.stream = stream
+        self.b.set_tiling(self.tiling)
+        w = np.ascontiguousarray(self.params, dtype=np.uint16)
+        K._check(K.lib().csp_batch_set_brancher(self.b.b, K.CSP_BR_LEARNED, w.ctypes.data_as(K._U16P)),
+                 "csp_batch_set_brancher")
+        self.b.bind(K.CSP_FIRST, stream)
+        self.rc, self.res = self.b.solve(K.CSP_FIRST, use_graph=True, bind=False)
+
+    def parity(self, st):
+        # the verdicts must equal first-fail's on every instance; SAT solutions are checked
+        from oracle import oracle as O
+        ok = [r["status"] for r in self.res] == [r["status"] for r in self.ff_res]
+        for m, r in zip(self.models, self.res):
+            if r["status"] == 1:
+                ok &= O.check_solution(O.OracleModel(m), self.sol[r["sol_offset"]:r["sol_offset"] + r["n"]])
+        return ok
+
+    def extra(self, K, st):
+        b = K.Batch([K.Csp(m) for m in self.models])
+        b.stream = self.b.stream
+        b.set_tiling(self.tiling)
+        b.bind(K.CSP_FIRST, self.b.stream)
+        times = []
+        for _ in range(4):
+            rc, self.ff_res = b.solve(K.CSP_FIRST, use_graph=True, bind=False)
+            times.append(b.stats()["ms"])
+        ff_ms = min(times[1:])
+        ff_nodes = sum(r["nodes"] for r in self.ff_res)
+        sat = sum(r["status"] == 1 for r in self.res)
+        return {"instances": self.count, "sat": sat, "unsat": self.count - sat,
+                "time_to_all_first_solutions_ms": st["ms"],
+                "first_fail_gpu_ms": ff_ms, "first_fail_gpu_nodes": ff_nodes,
+                "learned_nodes": st["nodes"], "speedup_vs_first_fail": ff_ms / st["ms"],
+                "training": {"logged_subtrees": self.cinfo["entries"], "train_nodes": self.cinfo["nodes"],
+                             "adam_steps": self.tinfo["steps"], "mse": self.tinfo["mse_per_epoch"][-1],
+                             "target_variance": self.tinfo["target_variance"],
+                             "collect_and_train_s": self.prep_s}}
+
+
 def make_workload(name):
     if name == "queens16":
         return Queens(16)
@@ -319,6 +402,8 @@ def make_workload(name):
         return Queens(14)
     if name == "rb4096":
         return RBBatch(4096)
+    if name == "rb_learned":
+        return LearnedRB()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -416,8 +501,8 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    parity = wl.parity(st)
     extra = wl.extra(K, st)
+    parity = wl.parity(st)
     smem_peak = K.probe_smem_bandwidth(stream)
     bpn = wl.bytes_per_node()
     kernel_ms = sum(kms) / len(kms)
@@ -453,7 +538,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="queens16", choices=["queens16", "queens14", "rb4096"])
+    ap.add_argument("--workload", default="queens16",
+                    choices=["queens16", "queens14", "rb4096", "rb_learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

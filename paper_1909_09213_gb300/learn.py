@@ -89,6 +89,29 @@ def train(data, epochs=8, batch=4096, lr=1e-3, seed=0, verbose=False):
     return params.cpu().numpy().view(np.uint16).copy(), info
 
 
+def learning_config(train_count=20000, eval_count=1024, epochs=8, sample=1, cap=8_000_000,
+                    eval_tiling=None, verbose=False):
+    """The learning configuration end to end: exhaustive, logged searches of `train_count`
+    model-RB instances (n = 30, d = 16), training, then first-solution searches of
+    `eval_count` held-out instances (n = 80, d = 20) with first-fail and with the network."""
+    from . import instances as I
+    t0 = time.time()
+    train_models = I.rb_batch(train_count, n_range=(30, 30), d_range=(16, 16), config_id=I.CFG_RB_TRAIN)
+    eval_models = I.rb_batch(eval_count, n_range=(80, 80), d_range=(20, 20), config_id=I.CFG_RB_EVAL)
+    gen_s = time.time() - t0
+    data, cinfo = collect(train_models, cap=cap, sample=sample)
+    if verbose:
+        print("collected", cinfo, flush=True)
+    params, tinfo = train(data, epochs=epochs, verbose=verbose)
+    ev = evaluate(eval_models, params, tiling=eval_tiling, reps=2)
+    same = ev["first_fail"]["status"] == ev["learned"]["status"]
+    return {"generate_s": gen_s, "collect": cinfo, "train": tinfo, "same_status": same,
+            "first_fail_ms": ev["first_fail"]["ms"], "learned_ms": ev["learned"]["ms"],
+            "first_fail_nodes": ev["first_fail"]["nodes"], "learned_nodes": ev["learned"]["nodes"],
+            "sat": sum(s == 1 for s in ev["learned"]["status"]), "eval": ev, "params": params,
+            "eval_models": eval_models}
+
+
 def evaluate(models, params_bf16, mode=K.CSP_FIRST, tiling=None, reps=1, stream=None):
     """Solve `models` as one batch with first-fail and with the learned brancher."""
     out = {}

@@ -86,6 +86,23 @@ def test_learned_first_mode_is_valid():
             assert O.check_solution(om, sols[0])
 
 
+def test_trained_network_gain_over_first_fail():
+    """The learning configuration at reduced size (2000 training instances n = 30, d = 16;
+    128 held-out instances n = 80, d = 20, first solution): the network trained on the
+    solver's own subtree logs must give the same verdict on every instance and explore fewer
+    nodes than first-fail.  The gain is an empirical measurement, not a pinned value."""
+    r = learn.learning_config(2000, 128, epochs=6)
+    assert r["same_status"]
+    ff, le = r["first_fail_nodes"], r["learned_nodes"]
+    print(f"\nlearned vs first-fail: nodes {le} vs {ff} ({ff / max(le, 1):.1f}x fewer), "
+          f"time {r['learned_ms']:.1f} ms vs {r['first_fail_ms']:.1f} ms")
+    assert le < ff
+    for m, res in zip(r["eval_models"], r["eval"]["learned"]["results"]):
+        if res["status"] == 1:
+            om = O.OracleModel(m)
+            assert O.check_solution(om, res["solution"])
+
+
 def test_subtree_logging_and_training():
     # the learning configuration's training instances (n = 30, d = 16): UNSAT proofs of
     # tens to hundreds of nodes each
