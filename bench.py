@@ -38,6 +38,11 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_09213_gb300", "csrc", f)
                   for f in ("search.cuh", "device.cuh", "internal.h", "kernels_w1.cu")]
 
 
+def note(msg):
+    """progress on stderr (the JSON line alone goes to stdout)"""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def kernel_digest() -> str:
     h = hashlib.sha1()
     for f in KERNEL_SOURCES:
@@ -220,18 +225,18 @@ class RBBatch:
 
     def bytes_per_node(self):
         """2 n W 4 + 4 (|D(x)| + 2) per table direction woken, from the oracle's event-driven
-        fixpoint on the first 32 instances (first-solution searches, 20 000 nodes at most)."""
+        fixpoint on the first 32 instances (first-solution searches, 2 000 nodes at most)."""
         from oracle import oracle as O
         nodes, by = 0, 0.0
         for m in self.models[:32]:
-            r = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1, W=1, node_limit=20000)
+            r = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1, W=1, node_limit=2000)
             nodes += r.nodes
             by += r.work_bytes + r.nodes * 2 * m.n * 4
         return by / max(nodes, 1)
 
     def setup(self, K, stream):
         from paper_1909_09213_gb300 import tune
-        self.tiling, self.tune_entry = tune.tune_batch(self.models, K.CSP_FIRST, calib=512)
+        self.tiling, self.tune_entry = tune.tune_batch(self.models, K.CSP_FIRST, calib=256, reps=1)
         self.probs = [K.Csp(m) for m in self.models]
         self.b = K.Batch(self.probs)
         self.b.stream = stream
@@ -286,14 +291,25 @@ class RBBatch:
                "time_to_all_first_solutions_ms": st["ms"],
                "tiling": {f: getattr(self.tiling, f) for f, _ in K.csp_tiling._fields_},
                "tuned_on": self.tune_entry.get("calib")}
-        # plain first-fail GPU search: the same instances one csp_solve at a time
+        # plain first-fail GPU search on a sample: the first 512 instances one csp_solve at a
+        # time, against the same 512 batched (one launch, same tiling)
+        sample = self.probs[:512]
+        note(f"plain first-fail on {len(sample)} instances")
         t0 = time.perf_counter()
         plain_nodes = 0
-        for p in self.probs:
+        for p in sample:
             rc, ps, _ = p.solve(K.CSP_FIRST)
             plain_nodes += ps["nodes"]
-        out["plain_first_fail_gpu_ms"] = 1e3 * (time.perf_counter() - t0)
-        out["plain_first_fail_gpu_nodes"] = plain_nodes
+        out["plain_first_fail_gpu_ms_sample512"] = 1e3 * (time.perf_counter() - t0)
+        out["plain_first_fail_gpu_nodes_sample512"] = plain_nodes
+        b = K.Batch(sample)
+        b.set_tiling(self.tiling)
+        b.stream = self.b.stream
+        b.bind(K.CSP_FIRST, self.b.stream)
+        t0 = time.perf_counter()
+        rc, res = b.solve(K.CSP_FIRST, use_graph=False, bind=False)
+        out["batched_gpu_ms_sample512"] = 1e3 * (time.perf_counter() - t0)
+        out["batched_gpu_kernel_ms_sample512"] = b.stats()["ms"]
         return out
 
     def _oracle_instances(self, start, budget_s):
@@ -444,7 +460,9 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     wl = make_workload(args.workload)
     stream = torch.cuda.Stream()
+    note(f"setup {args.workload}")
     wl.setup(K, stream)
+    note("setup done; warm-up and timed steps")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > 129 MB of L2
 
     def step():
@@ -486,6 +504,7 @@ def run_ours(args, rank, world, local_rank):
     value = nodes_all / (total_ms_max * 1e-3)
 
     # end to end through the public API: host-to-device copies, search, read-back
+    note("timed steps done; end-to-end steps")
     e2e_nodes, e2e_secs = 0, 0.0
     est = None
     for _ in range(max(3, args.steps // 2)):
@@ -501,6 +520,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
+    note("workload extras, parity, roofline, CPU baseline")
     extra = wl.extra(K, st)
     parity = wl.parity(st)
     smem_peak = K.probe_smem_bandwidth(stream)

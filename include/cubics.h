@@ -85,6 +85,7 @@ typedef struct {
     int64_t h2d_bytes;       /* host-to-device bytes of the last upload */
     int64_t d2h_bytes;       /* device-to-host bytes of the last collect */
     uint64_t wait_ns;        /* summed over workers: time spent waiting for work */
+    uint64_t rounds;         /* fixpoint rounds (propagation passes over the changed scopes) */
 } csp_stats_t;
 
 typedef struct {

@@ -64,6 +64,7 @@ struct Shape {
     int blocks = 0, warps = 0, lsm = 0, qcap = 0, stage_words = 0;
     int mlp_words = 0;     // staged brancher weights (learned ordering)
     int feat_words = 0;    // per-warp feature tile (learned ordering)
+    int list_words = 0;    // per-warp scheduled-table list (one-word tables)
     int warp_base = 0;     // shared-memory word where warp 0's area starts
     size_t smem = 0;
 };
@@ -72,7 +73,9 @@ struct Shape {
 // worker, cons the words of constraint data to stage in shared memory, nmax the largest
 // number of variables (feature tile rows when `learned`).
 int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batch, bool learned,
-               int nmax, Shape *s) {
+               int nmax, int ntab, Shape *s) {
+    // one-word tables are revised from a per-warp list of the scheduled ones
+    s->list_words = (W == 1 && ntab > 0) ? (ntab + 31) & ~31 : 0;
     s->warps = t.warps_per_block > 0 ? t.warps_per_block : 8;
     if (s->warps > 32) return CSP_EINVAL;
     s->mlp_words = learned ? CSP_MLP_PACKED_WORDS : 0;
@@ -81,7 +84,7 @@ int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batc
     lsm = std::max(2, std::min(lsm, depth));
     const int cons4 = (cons + 3) & ~3;
     auto bytes = [&](int l) {
-        return ((size_t)s->warps * (l * R + WS_WORDS + s->feat_words) + s->mlp_words) * 4;
+        return ((size_t)s->warps * (l * R + WS_WORDS + s->feat_words + s->list_words) + s->mlp_words) * 4;
     };
     size_t smem = bytes(lsm);
     while (smem > SMEM_MAX && lsm > 2) smem = bytes(--lsm);
@@ -360,7 +363,8 @@ int plan_single(csp *h, int32_t mode, int64_t cap, size_t *bytes, std::vector<ui
     const int depth = h->n + 1;
     const bool learned = h->brancher == CSP_BR_LEARNED;
     Shape s;
-    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, learned, h->n, &s);
+    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, learned, h->n,
+                        (int)B[H_N_TAB], &s);
     if (rc) return rc;
     h->shape = s;
     h->R = R;
@@ -390,6 +394,7 @@ void set_learned_args(SearchArgs &A, const Shape &s, bool learned, const uint8_t
     A.mlp = learned ? (const uint32_t *)(ws + o_packed) : nullptr;
     A.mlp_off = learned ? s.stage_words : -1;
     A.feat_words = s.feat_words;
+    A.list_words = s.list_words;
     A.warp_base = s.warp_base;
 }
 
@@ -443,6 +448,7 @@ void fill_stats(csp_stats_t *s, const GState &g, int64_t stored) {
     s->max_depth = g.max_depth;
     s->stored = stored;
     s->wait_ns = g.wait_ns;
+    s->rounds = g.rounds;
 }
 
 }  // namespace
@@ -782,7 +788,7 @@ struct csp_batch {
     int32_t mode = -1;
     size_t o_arena = 0, o_ioff = 0, o_soff = 0, o_g = 0, o_teams = 0, o_qseq = 0, o_qrec = 0,
            o_spill = 0, o_sols = 0, o_res = 0, o_mlp_params = 0, o_mlp_packed = 0;
-    int nmax = 1;
+    int nmax = 1, ntab_max = 0;
     int32_t brancher = CSP_BR_FIRST_FAIL;
     std::vector<uint16_t> mlp_params;
     float *logbuf = nullptr;                 // subtree logging (caller-owned device buffers)
@@ -801,7 +807,8 @@ int plan_batch(csp_batch *b, int32_t mode, size_t *bytes) {
     Shape s;
     const bool learned = b->brancher == CSP_BR_LEARNED;
     b->R = record_words(b->nmax * b->W, b->W, b->logbuf ? LOG_EXTRA : 0);
-    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, learned, b->nmax, &s);
+    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, learned, b->nmax,
+                        b->ntab_max, &s);
     if (rc) return rc;
     (void)mode;
     b->shape = s;
@@ -908,6 +915,7 @@ int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count) {
         b->inst_off.push_back((int64_t)b->arena.size());
         b->arena.insert(b->arena.end(), B.begin(), B.end());
         b->cons_max = std::max(b->cons_max, (int)B[H_CONS_WORDS]);
+        b->ntab_max = std::max(b->ntab_max, (int)B[H_N_TAB]);
         b->sol_off.push_back(sw);
         sw += h->n;
     }
@@ -933,6 +941,7 @@ int csp_batch_workspace_bytes(const csp_batch_t *bc, int32_t mode, size_t *bytes
     tmp.cons_max = bc->cons_max; tmp.arena = bc->arena; tmp.sol_words = bc->sol_words;
     tmp.tiling = bc->tiling; tmp.nmax = bc->nmax; tmp.brancher = bc->brancher;
     tmp.logbuf = bc->logbuf;
+    tmp.ntab_max = bc->ntab_max;
     return plan_batch(&tmp, mode, bytes);
 }
 

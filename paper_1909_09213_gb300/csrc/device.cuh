@@ -330,7 +330,7 @@ __device__ __forceinline__ bool for_scheduled(const IV<ST> &I, int evs, int mask
 // Returns true when some domain became empty.
 template <int W, bool ST>
 __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
-                         unsigned long long &evals) {
+                         unsigned long long &evals, unsigned long long &rounds, int list = -1) {
     const int lane = lane_id();
     const int n = I.n, NW = I.NW;
     if (I.flags & FLAG_TRIVIAL_FAIL) return true;
@@ -362,6 +362,7 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
             SM[chg + lane] = 0;
         }
         if (!__any_sync(FULLMASK, ev != 0u)) return false;
+        rounds++;
         __syncwarp();
         // 2. empty and fixed variables among them
         uint32_t fxw = 0;
@@ -407,7 +408,64 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
             if (__any_sync(FULLMASK, fail)) return true;
         }
         // 4. tables whose x or y changed
-        if (n_tab) {
+        if (n_tab && W == 1 && list >= 0) {
+            // One lane per table, over a compacted list of the scheduled tables, so every lane
+            // has a table.  D(x) keeps the values in the union of the columns C[b], b in D(y)
+            // (revised when D(y) changed); D(y) those in the union of the rows R[a], a in D(x)
+            // (revised when D(x) changed or was just revised).  A union stops growing once
+            // it covers the domain it filters.
+            const int tab = (int)I.w(H_OFF_TAB);
+            int cnt = 0;
+            for (int base = 0; base < n_tab; base += 32) {
+                const int t = base + lane;
+                uint32_t fl = 0;
+                if (t < n_tab) {
+                    fl = (ev_has(evs, (int)I.w(tab + 4 * t)) ? 1u : 0u) |
+                         (ev_has(evs, (int)I.w(tab + 4 * t + 1)) ? 2u : 0u);
+                }
+                const uint32_t mk = __ballot_sync(FULLMASK, fl != 0u);
+                if (fl) SM[list + cnt + __popc(mk & ((1u << lane) - 1u))] = (uint32_t)t | (fl << 30);
+                cnt += __popc(mk);
+            }
+            __syncwarp();
+            if (lane == 0) evals += cnt;
+            for (int i0 = 0; i0 < cnt; i0 += 32) {
+                const int i = i0 + lane;
+                if (i < cnt) {
+                    const uint32_t e = SM[list + i];
+                    const int te = tab + 4 * (int)(e & 0x3fffffffu);
+                    uint32_t fl = e >> 30;
+                    const int x = (int)I.w(te), y = (int)I.w(te + 1);
+                    uint32_t dx = SM[dom + x];
+                    const uint32_t dy = SM[dom + y];
+                    if (fl & 2u) {
+                        const int Cm = (int)I.w(te + 3);
+                        uint32_t acc = 0;
+                        for (uint32_t m = dy; m && (acc & dx) != dx; m &= m - 1) acc |= I.w(Cm + __ffs(m) - 1);
+                        const uint32_t kx = dx & acc;
+                        if (kx != dx) {
+                            const uint32_t old = atomicAnd(&SM[dom + x], kx);
+                            if (old & ~kx) mark_changed(chg, x);
+                            if ((old & kx) == 0u) fail = true;
+                            fl |= 1u;
+                            dx = kx;
+                        }
+                    }
+                    if ((fl & 1u) && dx) {
+                        const int Rm = (int)I.w(te + 2);
+                        uint32_t acc = 0;
+                        for (uint32_t m = dx; m && (acc & dy) != dy; m &= m - 1) acc |= I.w(Rm + __ffs(m) - 1);
+                        const uint32_t ky = dy & acc;
+                        if (ky != dy) {
+                            const uint32_t old = atomicAnd(&SM[dom + y], ky);
+                            if (old & ~ky) mark_changed(chg, y);
+                            if ((old & ky) == 0u) fail = true;
+                        }
+                    }
+                }
+            }
+            if (__any_sync(FULLMASK, fail)) return true;
+        } else if (n_tab) {
             const int tab = (int)I.w(H_OFF_TAB);
             for (int base = 0; base < n_tab; base += 32) {
                 const int t = base + lane;

@@ -15,7 +15,7 @@ constexpr int MAX_VARS = 1024;          // NW = ceil(n/32) <= 32 event words per
 constexpr int MAX_W = 8;                // 256-value window
 constexpr int HDR_WORDS = 32;
 constexpr uint32_t FLAG_TRIVIAL_FAIL = 1u;  // a row with no terms and rhs < 0
-constexpr int WS_WORDS = 88;            // per-warp shared bookkeeping (events, counters)
+constexpr int WS_WORDS = 92;            // per-warp shared bookkeeping (events, counters)
 
 enum Hdr {
     H_N = 0, H_W, H_LO0, H_S, H_NW, H_FLAGS,
@@ -66,11 +66,12 @@ struct GState {               // counters of one launch
     unsigned long long stored;        // solution slots taken
     unsigned long long node_progress; // for the node limit
     unsigned long long wait_ns;       // summed over workers: time spent waiting for work
+    unsigned long long rounds;        // fixpoint rounds
     int32_t max_depth;
     int32_t status;                   // 0 ok, else CSP_E*
     int32_t abort;                    // global stop
     int32_t ticket;                   // next batch instance
-    int32_t pad[22];
+    int32_t pad[20];
 };
 
 struct InstResult {
@@ -110,6 +111,7 @@ struct SearchArgs {
     int32_t mlp_off;          // SM word offset of the staged weights, -1 = first-fail
     int32_t feat_words;       // per-warp words of the learned brancher's feature tile
     int32_t warp_base;        // SM word offset of warp 0's area
+    int32_t list_words;       // per-warp words of the scheduled-table list (one-word tables)
     int32_t log_extra;        // subtree logging: LOG_EXTRA extra record words, else 0
     uint32_t log_sample;      // log one completed level in log_sample (hash of worker, count)
     float *logbuf;            // log entries of 17 floats: 16 features, log2 subtree nodes

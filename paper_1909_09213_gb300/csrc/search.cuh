@@ -36,6 +36,8 @@ struct WarpShared {
     int64_t sol_off;
     long long wait_ns;    // time spent waiting for a record
     int32_t maxd, pad;
+    unsigned long long rounds;   // fixpoint rounds
+    int32_t pad2[2];
 };
 static_assert(sizeof(WarpShared) == 4 * WS_WORDS, "WarpShared size must match WS_WORDS");
 
@@ -397,8 +399,9 @@ struct Worker {
             p_qlen = ld_volatile(&T->tail) - ld_volatile(&T->head);
         }
         if ((tick & 63) == 0) check_limits();
-        unsigned long long ev = 0;
-        const bool failed = fixpoint<W, ST>(I, C, chg(), evs(), full, ev);
+        unsigned long long ev = 0, rnd = 0;
+        const int list = SA.list_words ? wso + WS_WORDS + SA.feat_words : -1;
+        const bool failed = fixpoint<W, ST>(I, C, chg(), evs(), full, ev, rnd, list);
         // a root shared by several ranks (its children dealt round-robin) counts on rank 0 only
         const bool split_root = full && !SA.batch && SA.nparts > 1;
         const bool counted = !split_root || SA.part == 0;
@@ -406,6 +409,7 @@ struct Worker {
             WarpShared &w = ws();
             w.nodes++;
             w.evals += ev;
+            w.rounds += rnd;
         }
         stop = __shfl_sync(FULLMASK, p_stop, 0);
         if (failed) {
@@ -561,6 +565,7 @@ struct Worker {
             w.maxd = 0;
             w.sol_off = 0;
             w.wait_ns = 0;
+            w.rounds = 0;
             w.t_start = global_ns();
         }
         __syncwarp();
@@ -579,6 +584,7 @@ struct Worker {
             atomicAdd(&g->steals, w.steals);
             atomicAdd(&g->spills, w.spills);
             atomicAdd(&g->wait_ns, (unsigned long long)w.wait_ns);
+            atomicAdd(&g->rounds, w.rounds);
             atomicMax(&g->max_depth, w.maxd);
         }
     }
@@ -601,7 +607,7 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
     __shared__ int s_inst, s_team;
     if (threadIdx.x == 0) SA = Ap;
     __syncthreads();
-    const int per_warp = SA.lsm * SA.rmax + WS_WORDS + SA.feat_words;
+    const int per_warp = SA.lsm * SA.rmax + WS_WORDS + SA.feat_words + SA.list_words;
     if (SA.mlp_off >= 0) {           // the brancher's weights, staged once per block
         for (int i = threadIdx.x; i < PK_WORDS; i += blockDim.x) SM[SA.mlp_off + i] = __ldg(SA.mlp + i);
         __syncthreads();
@@ -731,7 +737,8 @@ __global__ void __launch_bounds__(256) propagate_kernel(PropArgs P) {
         const uint32_t *src = P.din + (size_t)s * I.S;
         for (int k = lane; k < I.S; k += 32) SM[dom + k] = src[k];
         __syncwarp();
-        const bool failed = fixpoint<W, ST>(I, dom, chg, evs, true, evals);
+        unsigned long long rounds = 0;
+        const bool failed = fixpoint<W, ST>(I, dom, chg, evs, true, evals, rounds);
         __syncwarp();
         uint32_t *dst = P.dout + (size_t)s * I.S;
         for (int k = lane; k < I.S; k += 32) dst[k] = SM[dom + k];

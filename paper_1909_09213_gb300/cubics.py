@@ -43,7 +43,8 @@ class csp_stats_t(C.Structure):
                 ("prop_evals", C.c_uint64), ("steals", C.c_uint64), ("spills", C.c_uint64),
                 ("max_depth", C.c_int32), ("status", C.c_int32), ("ms", C.c_double),
                 ("stored", C.c_int64), ("workers", C.c_int32), ("blocks", C.c_int32),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("wait_ns", C.c_uint64)]
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("wait_ns", C.c_uint64),
+                ("rounds", C.c_uint64)]
 
 
 class csp_result(C.Structure):
