@@ -312,16 +312,17 @@ class RBBatch:
         out["batched_gpu_kernel_ms_sample512"] = b.stats()["ms"]
         return out
 
-    def _oracle_instances(self, start, budget_s):
+    def _oracle_instances(self, start, budget_s, node_limit=100_000):
         from oracle import oracle as O
         nodes, secs, k = 0, 0.0, start
         while secs < budget_s and k < self.count:
             t = time.perf_counter()
-            r = O.solve(O.OracleModel(self.models[k]), mode=1, cap=1, variant=1)
+            r = O.solve(O.OracleModel(self.models[k]), mode=1, cap=1, variant=1, node_limit=node_limit)
             secs += time.perf_counter() - t
             nodes += r.nodes
             k += 1
-        return nodes, secs, f"model-RB instances {start}..{k - 1} of the batch, first solution each"
+        return nodes, secs, (f"instances {start}..{k - 1} of the batch, first solution each "
+                             f"(at most {node_limit} nodes each)")
 
     def cpu_sample(self):
         return self._oracle_instances(0, 12.0)
@@ -411,6 +412,82 @@ class LearnedRB(RBBatch):
                              "collect_and_train_s": self.prep_s}}
 
 
+class LinAdBatch(RBBatch):
+    """256 mixed linear/alldifferent instances (200 vars on 0..255, 8-word domains, 60 rows of
+    5-20 terms, 20 alldifferent groups of 10), first solution each, one launch per step, a
+    node limit per instance (instances that reach it are reported undecided)."""
+
+    NODE_LIMIT = 2_000_000
+
+    def __init__(self, count=256):
+        from paper_1909_09213_gb300 import instances as I
+        self.count = count
+        self.models = I.linad_batch(count)
+        self.desc = (f"{count} mixed instances: 200 vars on 0..255 (8 words), 60 int_lin_le rows of "
+                     f"5-20 terms, 20 alldifferent groups of 10, rhs theta {I.LINAD_THETA}, first "
+                     f"solution, {self.NODE_LIMIT} nodes at most per instance")
+        self.profile = "search_kernel_linad256.md"
+
+    def golden(self):
+        return None
+
+    def bytes_per_node(self):
+        """2 n W 4 + 4 W (2k + changed) per row wake + 4 W 2k per alldifferent wake, from the
+        oracle's event-driven fixpoint on the first solution search of 2 instances (500 nodes)"""
+        from oracle import oracle as O
+        nodes, by = 0, 0.0
+        for m in self.models[:2]:
+            r = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1, W=8, node_limit=500)
+            nodes += r.nodes
+            by += r.work_bytes + r.nodes * 2 * m.n * 8 * 4
+        return by / max(nodes, 1)
+
+    def setup(self, K, stream):
+        self.tiling = K.tiling(warps_per_block=4, smem_levels=4)
+        self.tune_entry = {"calib": None}
+        self.lim = K.limits(node_limit=self.NODE_LIMIT)
+        self.probs = [K.Csp(m) for m in self.models]
+        self.b = K.Batch(self.probs)
+        self.b.stream = stream
+        self.b.set_tiling(self.tiling)
+        self.b.bind(K.CSP_FIRST, stream)
+        self.rc, self.res = self.b.solve(K.CSP_FIRST, lim=self.lim, use_graph=True, bind=False)
+
+    def launch(self, K):
+        import ctypes
+        K._check(K.lib().csp_batch_launch(self.b.b, ctypes.byref(self.lim), 1), "csp_batch_launch")
+
+    def e2e_step(self, K):
+        rc, res = self.b.solve(K.CSP_FIRST, lim=self.lim, use_graph=True, bind=False)
+        st = self.b.stats()
+        st["nodes"] = sum(r["nodes"] for r in res)
+        st["h2d_bytes"] = 0
+        st["d2h_bytes"] = self.count * 40 + 4 * K.lib().csp_batch_solution_words(self.b.b)
+        return st
+
+    def parity(self, st):
+        # every reported solution satisfies every constraint (oracle check)
+        from oracle import oracle as O
+        ok = True
+        for m, r in zip(self.models, self.res):
+            if r["status"] == 1:
+                ok &= O.check_solution(O.OracleModel(m), self.sol[r["sol_offset"]:r["sol_offset"] + r["n"]])
+        return ok
+
+    def extra(self, K, st):
+        sat = sum(r["status"] == 1 for r in self.res)
+        unsat = sum(r["status"] == 0 for r in self.res)
+        return {"instances": self.count, "sat": sat, "unsat": unsat,
+                "undecided_at_node_limit": self.count - sat - unsat,
+                "time_to_all_first_solutions_ms": st["ms"]}
+
+    def cpu_sample(self):
+        return self._oracle_instances(0, 12.0)
+
+    def reference_step(self):
+        return self._oracle_instances(0, 1.5)
+
+
 def make_workload(name):
     if name == "queens16":
         return Queens(16)
@@ -418,6 +495,8 @@ def make_workload(name):
         return Queens(14)
     if name == "rb4096":
         return RBBatch(4096)
+    if name == "linad256":
+        return LinAdBatch(256)
     if name == "rb_learned":
         return LearnedRB()
     raise SystemExit(f"unknown workload {name}")
@@ -559,7 +638,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="queens16",
-                    choices=["queens16", "queens14", "rb4096", "rb_learned"])
+                    choices=["queens16", "queens14", "rb4096", "rb_learned", "linad256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -52,7 +52,8 @@ typedef struct csp csp_t;
 typedef struct csp_batch csp_batch_t;
 
 typedef struct {
-    int64_t node_limit;      /* stop after about this many nodes; 0 = none */
+    int64_t node_limit;      /* stop after about this many nodes (batches: per instance, which
+                                then reports CSP_ELIMIT); 0 = none */
     int64_t time_limit_ns;   /* stop after this device time; 0 = none */
     int64_t wait_limit_ns;   /* bound on every device-side wait; 0 = 60 s */
     int32_t flags;           /* CSP_F_* */

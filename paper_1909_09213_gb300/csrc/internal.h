@@ -56,9 +56,10 @@ struct Team {                 // one work-sharing group (whole grid or one block
     int32_t work;             // records queued or being explored
     int32_t idle;             // workers waiting for a record
     uint32_t head, tail;      // queue positions
-    int32_t found;            // CSP_FIRST: a solution was recorded
+    int32_t found;            // 1: CSP_FIRST solution recorded; 2: the instance hit its node limit
     int32_t inst;             // instance index (batch mode)
-    int32_t pad[26];          // one 128-byte line per team
+    unsigned long long progress;  // batch mode: nodes spent on the instance (limit accounting)
+    int32_t pad[24];          // one 128-byte line per team
 };
 
 struct GState {               // counters of one launch

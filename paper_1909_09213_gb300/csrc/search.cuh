@@ -158,14 +158,19 @@ struct Worker {
         int s = 0;
         if (lane_id() == 0) {
             s = ld_volatile(&SA.g->abort);
-            if (SA.mode == 1) s |= ld_volatile(&T->found);
+            if (SA.mode == 1 || SA.batch) s |= ld_volatile(&T->found);
         }
         return s;
     }
 
+    // Node and time limits, every 64 nodes.  In batch mode the node limit is per instance:
+    // the team's instance stops (found = 2) and the others go on.
     __device__ void check_limits() {
         if (lane_id() == 0) {
-            if (SA.node_limit > 0) {
+            if (SA.node_limit > 0 && SA.batch) {
+                const unsigned long long tot = atomicAdd(&T->progress, 64ull) + 64ull;
+                if ((long long)tot >= SA.node_limit) atomicCAS(&T->found, 0, 2);
+            } else if (SA.node_limit > 0) {
                 const unsigned long long tot = atomicAdd(&SA.g->node_progress, 64ull) + 64ull;
                 if ((long long)tot >= SA.node_limit) {
                     atomicCAS(&SA.g->status, 0, CSP_ELIMIT_);
@@ -690,6 +695,7 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
             if (lane == 0) {
                 T->inst = i;
                 T->found = 0;
+                T->progress = 0;
                 __threadfence();
                 atomicExch(&T->work, 1);
             }
@@ -710,7 +716,10 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
             const int st = ld_volatile(&SA.g->status);
             __threadfence();
             const unsigned long long sols = *(volatile unsigned long long *)&r.solutions;
-            r.status = ld_volatile(&T->found) || sols > 0 ? 1 : (st != 0 ? st : 0);
+            const int fnd = ld_volatile(&T->found);
+            // FIRST: a solution settles the verdict.  ALL: an instance stopped at its node limit
+            // has an incomplete count, so it is undecided even if it found solutions.
+            r.status = fnd == 1 ? 1 : fnd == 2 ? CSP_ELIMIT_ : sols > 0 ? 1 : (st != 0 ? st : 0);
             r.n = (int)ib[H_N];
             r.sol_offset = SA.sol_off ? SA.sol_off[i] : 0;
         }

@@ -339,6 +339,21 @@ def test_batch_all_counts_and_graph_replay():
     assert strip(res_g) == strip(res) == strip(res_g2)
 
 
+def test_batch_node_limit_is_per_instance():
+    """A batch node limit stops only the instances that reach it: they report CSP_ELIMIT and
+    the others keep their exact verdicts."""
+    easy = _rb_small(24, first=1300)
+    hard = I.queens(13)                                     # 4.2 M nodes in all-solution mode
+    models = easy[:12] + [hard] + easy[12:]
+    b = K.Batch([K.Csp(m) for m in models])
+    rc, res = b.solve(K.CSP_ALL, lim=K.limits(node_limit=100_000))
+    assert rc == 0
+    assert res[12]["status"] == K.CSP_ELIMIT
+    for m, r in zip(easy, res[:12] + res[13:]):
+        o = O.solve(O.OracleModel(m), variant=1)
+        assert (r["status"], r["solutions"], r["nodes"]) == (o.status, o.solutions, o.nodes), m.name
+
+
 def test_batch_tilings_do_not_change_results():
     models = _rb_small(40, first=900)
     probs = [K.Csp(m) for m in models]
