@@ -86,8 +86,14 @@ int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batc
     auto bytes = [&](int l) {
         return ((size_t)s->warps * (l * R + WS_WORDS + s->feat_words + s->list_words) + s->mlp_words) * 4;
     };
+    // a power of two, so that a level's slot is its index masked: rounded up when the whole
+    // stack was to fit (and still fits), down otherwise
+    int p2 = 2;
+    while (p2 < lsm) p2 <<= 1;
+    const bool up = lsm == depth && bytes(p2) + (size_t)cons4 * 4 <= SMEM_MAX;
+    lsm = (p2 == lsm || up) ? p2 : p2 >> 1;
     size_t smem = bytes(lsm);
-    while (smem > SMEM_MAX && lsm > 2) smem = bytes(--lsm);
+    while (smem > SMEM_MAX && lsm > 2) smem = bytes(lsm >>= 1);
     if (smem > SMEM_MAX) return CSP_ETOOBIG;
     s->stage_words = (smem + (size_t)cons4 * 4 <= SMEM_MAX) ? cons4 : 0;
     s->warp_base = s->stage_words + s->mlp_words;
@@ -334,6 +340,7 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
     while (B.size() & 63) B.push_back(0u);
     B[H_TOTAL] = (uint32_t)B.size();
     B[H_R] = (uint32_t)record_words(S, W);
+    if (h->lin.empty() && h->ad.empty() && h->tab.empty()) flags |= FLAG_NE_ONLY;
     B[H_FLAGS] = flags;
 }
 

@@ -324,6 +324,79 @@ __device__ __forceinline__ bool for_scheduled(const IV<ST> &I, int evs, int mask
 
 // ------------------------------------------------------------------ fixpoint
 
+// The fixpoint of a problem with int_ne constraints only and one-word domains.  A newly fixed
+// variable removes one value from each neighbour; a neighbour left with a single value is
+// newly fixed in turn.  With one word per domain the atomicAnd's return value tells exactly
+// which removal left one value (or none), so the next round's work is known without
+// re-reading the domains.  SM[chg] holds the newly fixed variables (NW words); with full =
+// true it is computed here from the domains.  Returns true when some domain became empty.
+template <bool ST>
+__device__ bool fixpoint_ne1(const IV<ST> &I, int dom, int chg, bool full, unsigned long long &evals,
+                             unsigned long long &rounds) {
+    const int lane = lane_id();
+    const int n = I.n, NW = I.NW;
+    if (full) {
+        const int nun = (int)I.w(H_N_UN);
+        const int un = (int)I.w(H_OFF_UN);
+        for (int i = lane; i < nun; i += 32) {
+            const uint32_t u = I.w(un + i);
+            atomicAnd(&SM[dom + (int)(u & 0xffffu)], ~(1u << (u >> 16)));
+        }
+        __syncwarp();
+        bool bad = false;
+        for (int c = 0; c < NW; ++c) {
+            const int v = (c << 5) + lane;
+            const uint32_t d = v < n ? SM[dom + v] : 3u;
+            bad |= d == 0u;
+            const uint32_t f = __ballot_sync(FULLMASK, v < n && d != 0u && (d & (d - 1u)) == 0u);
+            if (lane == 0) SM[chg + c] = f;
+        }
+        if (__any_sync(FULLMASK, bad)) return true;
+        __syncwarp();
+    }
+    const int adj_start = (int)I.w(H_OFF_ADJ_START);
+    const int adj = (int)I.w(H_OFF_ADJ);
+    for (;;) {
+        uint32_t fx = 0;
+        if (lane < NW) {
+            fx = SM[chg + lane];
+            SM[chg + lane] = 0u;
+        }
+        if (!__any_sync(FULLMASK, fx != 0u)) return false;
+        rounds++;
+        __syncwarp();
+        bool fail = false;
+        for (int c = 0; c < NW; ++c) {
+            uint32_t f = __shfl_sync(FULLMASK, fx, c);
+            while (f) {
+                const int v = (c << 5) + __ffs(f) - 1;
+                f &= f - 1;
+                evals++;
+                const uint32_t dv = SM[dom + v];
+                if (dv == 0u) { fail = true; continue; }   // its value was removed meanwhile
+                const int val = __ffs(dv) - 1;
+                const int e0 = (int)I.w(adj_start + v), e1 = (int)I.w(adj_start + v + 1);
+                for (int e = e0 + lane; e < e1; e += 32) {
+                    const uint32_t ent = I.w(adj + e);
+                    const int t = (int)(ent & 0xffffu);
+                    const int tb = val + (int)(int16_t)(ent >> 16);
+                    if ((unsigned)tb < 32u) {
+                        const uint32_t m = 1u << tb;
+                        const uint32_t old = atomicAnd(&SM[dom + t], ~m);
+                        if (old & m) {
+                            const uint32_t nw = old & ~m;
+                            if (nw == 0u) fail = true;
+                            else if ((nw & (nw - 1u)) == 0u) atomicOr(&SM[chg + (t >> 5)], 1u << (t & 31));
+                        }
+                    }
+                }
+            }
+        }
+        if (__any_sync(FULLMASK, fail)) return true;
+        __syncwarp();
+    }
+}
+
 // Propagates the node at SM[dom] (S words) to its fixpoint.  SM[chg] (NW words) holds the
 // variables changed since the last fixpoint; with full = true every variable counts as
 // changed and unary constraints are applied first.  SM[evs] is NW words of scratch.
@@ -334,6 +407,7 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
     const int lane = lane_id();
     const int n = I.n, NW = I.NW;
     if (I.flags & FLAG_TRIVIAL_FAIL) return true;
+    if (W == 1 && (I.flags & FLAG_NE_ONLY)) return fixpoint_ne1<ST>(I, dom, chg, full, evals, rounds);
     if (full) {
         if (lane < NW) {
             const int rem = n - (lane << 5);

@@ -15,6 +15,7 @@ constexpr int MAX_VARS = 1024;          // NW = ceil(n/32) <= 32 event words per
 constexpr int MAX_W = 8;                // 256-value window
 constexpr int HDR_WORDS = 32;
 constexpr uint32_t FLAG_TRIVIAL_FAIL = 1u;  // a row with no terms and rhs < 0
+constexpr uint32_t FLAG_NE_ONLY = 2u;       // int_ne constraints only (no lin, alldiff, table)
 constexpr int WS_WORDS = 92;            // per-warp shared bookkeeping (events, counters)
 
 enum Hdr {

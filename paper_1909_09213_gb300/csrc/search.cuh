@@ -131,7 +131,8 @@ struct Worker {
     __device__ __forceinline__ uint32_t *spill(int k) const {
         return SA.spill + ((size_t)gw * SA.depth + k) * SA.rmax;
     }
-    __device__ __forceinline__ int slot(int k) const { return slots + (k % lsm) * R; }
+    // lsm is a power of two
+    __device__ __forceinline__ int slot(int k) const { return slots + (k & (lsm - 1)) * R; }
 
     // make the shared slot of level k (== top) free
     __device__ void make_room(int k) {
