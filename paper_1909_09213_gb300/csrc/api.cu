@@ -14,9 +14,10 @@
 #include "internal.h"
 
 namespace cubics {
-cudaError_t launch_search(int W, bool staged, const SearchArgs &A, int blocks, int threads,
-                          size_t smem, cudaStream_t st);
-cudaError_t occupancy_search(int W, bool staged, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_search(int W, bool staged, bool ext, const SearchArgs &A, int blocks,
+                          int threads, size_t smem, cudaStream_t st);
+cudaError_t occupancy_search(int W, bool staged, bool ext, int threads, size_t smem,
+                             int *blocks_per_sm);
 cudaError_t launch_init_single(const SearchArgs &A, cudaStream_t st);
 cudaError_t launch_init_batch(const SearchArgs &A, int teams, cudaStream_t st);
 cudaError_t launch_propagate(int W, bool staged, const PropArgs &P, int blocks, int threads,
@@ -62,6 +63,7 @@ DeviceInfo device_info() {
 
 struct Shape {
     int blocks = 0, warps = 0, lsm = 0, qcap = 0, stage_words = 0;
+    bool ext = false;      // kernel with the learned brancher and subtree logging
     int mlp_words = 0;     // staged brancher weights (learned ordering)
     int feat_words = 0;    // per-warp feature tile (learned ordering)
     int list_words = 0;    // per-warp scheduled-table list (one-word tables)
@@ -73,7 +75,8 @@ struct Shape {
 // worker, cons the words of constraint data to stage in shared memory, nmax the largest
 // number of variables (feature tile rows when `learned`).
 int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batch, bool learned,
-               int nmax, int ntab, Shape *s) {
+               bool logging, int nmax, int ntab, Shape *s) {
+    s->ext = learned || logging;
     // one-word tables are revised from a per-warp list of the scheduled ones
     s->list_words = (W == 1 && ntab > 0) ? (ntab + 31) & ~31 : 0;
     s->warps = t.warps_per_block > 0 ? t.warps_per_block : 8;
@@ -102,19 +105,20 @@ int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batc
     int q = t.queue_records > 0 ? t.queue_records : (batch ? 64 : 4096);
     if (q & (q - 1)) return CSP_EINVAL;
     s->qcap = q;
+    // resident blocks per SM; 0 when a block of this many warps exceeds the kernel's
+    // registers.  An explicit grid needs no device to be planned.
+    int bps = 0;
+    const cudaError_t oe =
+        occupancy_search(W, s->stage_words > 0, s->ext, s->warps * 32, s->smem, &bps);
+    if (oe != cudaSuccess) cudaGetLastError();
+    if (oe == cudaSuccess && bps < 1) return CSP_EINVAL;
     if (t.blocks > 0) {
         s->blocks = t.blocks;
-    } else {
-        DeviceInfo di = device_info();
-        if (!di.ok) return CSP_ECUDA;
-        int bps = 0;
-        if (occupancy_search(W, s->stage_words > 0, s->warps * 32, s->smem, &bps) != cudaSuccess ||
-            bps < 1) {
-            cudaGetLastError();
-            return CSP_ECUDA;
-        }
-        s->blocks = di.sms * bps;
+        return CSP_OK;
     }
+    DeviceInfo di = device_info();
+    if (!di.ok || oe != cudaSuccess) return CSP_ECUDA;
+    s->blocks = di.sms * bps;
     return CSP_OK;
 }
 
@@ -370,8 +374,8 @@ int plan_single(csp *h, int32_t mode, int64_t cap, size_t *bytes, std::vector<ui
     const int depth = h->n + 1;
     const bool learned = h->brancher == CSP_BR_LEARNED;
     Shape s;
-    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, learned, h->n,
-                        (int)B[H_N_TAB], &s);
+    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, learned, false,
+                        h->n, (int)B[H_N_TAB], &s);
     if (rc) return rc;
     h->shape = s;
     h->R = R;
@@ -673,8 +677,8 @@ int csp_launch(csp_t *h, const csp_limits *lim) {
     if (e == cudaSuccess) e = launch_init_single(A, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess)
-        e = launch_search(h->W, h->shape.stage_words > 0, A, h->shape.blocks, h->shape.warps * 32,
-                          h->shape.smem, h->stream);
+        e = launch_search(h->W, h->shape.stage_words > 0, h->shape.ext, A, h->shape.blocks,
+                          h->shape.warps * 32, h->shape.smem, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
     h->stats.workers = h->shape.blocks * h->shape.warps;
     h->stats.blocks = h->shape.blocks;
@@ -814,8 +818,8 @@ int plan_batch(csp_batch *b, int32_t mode, size_t *bytes) {
     Shape s;
     const bool learned = b->brancher == CSP_BR_LEARNED;
     b->R = record_words(b->nmax * b->W, b->W, b->logbuf ? LOG_EXTRA : 0);
-    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, learned, b->nmax,
-                        b->ntab_max, &s);
+    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, learned,
+                        b->logbuf != nullptr, b->nmax, b->ntab_max, &s);
     if (rc) return rc;
     (void)mode;
     b->shape = s;
@@ -884,8 +888,8 @@ cudaError_t enqueue_batch(csp_batch *b, const SearchArgs &A) {
         e = cudaMemsetAsync(b->ws + b->o_res, 0, b->hs.size() * sizeof(InstResult), b->stream);
     if (e == cudaSuccess) e = launch_init_batch(A, b->shape.blocks, b->stream);
     if (e == cudaSuccess)
-        e = launch_search(b->W, b->shape.stage_words > 0, A, b->shape.blocks, b->shape.warps * 32,
-                          b->shape.smem, b->stream);
+        e = launch_search(b->W, b->shape.stage_words > 0, b->shape.ext, A, b->shape.blocks,
+                          b->shape.warps * 32, b->shape.smem, b->stream);
     return e;
 }
 
@@ -1025,8 +1029,8 @@ int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph) {
         if (!b->graph || b->graph_mode != b->mode || !same_limits(L, b->graph_lim)) {
             drop_graph(b);
             int bps = 0;   // sets the kernel's shared-memory attribute outside the capture
-            e = occupancy_search(b->W, b->shape.stage_words > 0, b->shape.warps * 32, b->shape.smem,
-                                 &bps);
+            e = occupancy_search(b->W, b->shape.stage_words > 0, b->shape.ext, b->shape.warps * 32,
+                                 b->shape.smem, &bps);
             cudaGraph_t g = nullptr;
             if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
@@ -1178,8 +1182,8 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_team, 0, sizeof(Team), h->stream);
     if (e == cudaSuccess) e = launch_init_single(A, h->stream);
     if (e == cudaSuccess)
-        e = launch_search(h->W, h->shape.stage_words > 0, A, h->shape.blocks, h->shape.warps * 32,
-                          h->shape.smem, h->stream);
+        e = launch_search(h->W, h->shape.stage_words > 0, h->shape.ext, A, h->shape.blocks,
+                          h->shape.warps * 32, h->shape.smem, h->stream);
     GState g;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&g, h->ws + h->o_g, sizeof(g), cudaMemcpyDeviceToHost, h->stream);

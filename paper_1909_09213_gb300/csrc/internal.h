@@ -55,13 +55,23 @@ constexpr int LOG_EXTRA = 1 + 16;
 
 struct Team {                 // one work-sharing group (whole grid or one block)
     int32_t work;             // records queued or being explored
-    int32_t idle;             // workers waiting for a record
-    uint32_t head, tail;      // queue positions
     int32_t found;            // 1: CSP_FIRST solution recorded; 2: the instance hit its node limit
     int32_t inst;             // instance index (batch mode)
+    int32_t pad0;
     unsigned long long progress;  // batch mode: nodes spent on the instance (limit accounting)
-    int32_t pad[24];          // one 128-byte line per team
+    int32_t pad1[26];
+    uint32_t head;            // consumer tickets (own 128-byte line)
+    int32_t pad2[31];
+    uint32_t tail;            // producer positions (own 128-byte line)
+    int32_t pad3[31];
+    int32_t need;             // waiting workers not yet promised a record (own line)
+    int32_t pad4[31];
+    // sizes of the subtrees taken from the queue, by the share of unfixed variables in the
+    // record (bin u * UBINS / (n + 1)): low 32 bits count them, high 32 bits count the small ones
+    unsigned long long ustat[32];
 };
+constexpr int UBINS = 32;
+static_assert(sizeof(Team) == 768, "Team is six 128-byte lines");
 
 struct GState {               // counters of one launch
     unsigned long long nodes, fails, solutions, hsum, hxor, evals, steals, spills;

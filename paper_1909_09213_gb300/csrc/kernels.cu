@@ -7,31 +7,45 @@ namespace cubics {
 #define CUBICS_DECLARE_WIDTH(WW)                                                             \
     cudaError_t launch_search_w##WW(bool, const SearchArgs &, int, int, size_t, cudaStream_t); \
     cudaError_t occupancy_w##WW(bool, int, size_t, int *);                                   \
+    cudaError_t launch_search_ext_w##WW(bool, const SearchArgs &, int, int, size_t,          \
+                                        cudaStream_t);                                       \
+    cudaError_t occupancy_ext_w##WW(bool, int, size_t, int *);                               \
     cudaError_t launch_prop_w##WW(bool, const PropArgs &, int, int, size_t, cudaStream_t);
 CUBICS_DECLARE_WIDTH(1)
 CUBICS_DECLARE_WIDTH(2)
 CUBICS_DECLARE_WIDTH(4)
 CUBICS_DECLARE_WIDTH(8)
 
-cudaError_t launch_search(int W, bool staged, const SearchArgs &A, int blocks, int threads,
-                          size_t smem, cudaStream_t st) {
+// ext: the kernel with the learned brancher and subtree logging
+cudaError_t launch_search(int W, bool staged, bool ext, const SearchArgs &A, int blocks,
+                          int threads, size_t smem, cudaStream_t st) {
+#define CUBICS_CASE(WW)                                                                      \
+    case WW:                                                                                 \
+        return ext ? launch_search_ext_w##WW(staged, A, blocks, threads, smem, st)           \
+                   : launch_search_w##WW(staged, A, blocks, threads, smem, st);
     switch (W) {
-    case 1: return launch_search_w1(staged, A, blocks, threads, smem, st);
-    case 2: return launch_search_w2(staged, A, blocks, threads, smem, st);
-    case 4: return launch_search_w4(staged, A, blocks, threads, smem, st);
-    case 8: return launch_search_w8(staged, A, blocks, threads, smem, st);
+    CUBICS_CASE(1)
+    CUBICS_CASE(2)
+    CUBICS_CASE(4)
+    CUBICS_CASE(8)
     default: return cudaErrorInvalidValue;
     }
+#undef CUBICS_CASE
 }
 
-cudaError_t occupancy_search(int W, bool staged, int threads, size_t smem, int *bps) {
+cudaError_t occupancy_search(int W, bool staged, bool ext, int threads, size_t smem, int *bps) {
+#define CUBICS_CASE(WW)                                                                      \
+    case WW:                                                                                 \
+        return ext ? occupancy_ext_w##WW(staged, threads, smem, bps)                         \
+                   : occupancy_w##WW(staged, threads, smem, bps);
     switch (W) {
-    case 1: return occupancy_w1(staged, threads, smem, bps);
-    case 2: return occupancy_w2(staged, threads, smem, bps);
-    case 4: return occupancy_w4(staged, threads, smem, bps);
-    case 8: return occupancy_w8(staged, threads, smem, bps);
+    CUBICS_CASE(1)
+    CUBICS_CASE(2)
+    CUBICS_CASE(4)
+    CUBICS_CASE(8)
     default: return cudaErrorInvalidValue;
     }
+#undef CUBICS_CASE
 }
 
 cudaError_t launch_propagate(int W, bool staged, const PropArgs &P, int blocks, int threads,

@@ -42,24 +42,30 @@ struct WarpShared {
 static_assert(sizeof(WarpShared) == 4 * WS_WORDS, "WarpShared size must match WS_WORDS");
 
 // ------------------------------------------------------------------ work queue
-// Bounded multi-producer multi-consumer ring (per-slot sequence numbers).  Lane 0 claims a
-// position; the warp copies the record; a release store of the sequence publishes it.
+// Bounded ring of records with a sequence word per slot.  Producers claim a position with
+// a compare-and-swap on the tail (a full queue makes the push fail, and the donor keeps its
+// values).  Consumers take a ticket with a fetch-and-add on the head, which never fails,
+// and wait for their own slot to be filled: waiting workers poll distinct words instead of
+// all racing for the head, and they are served in ticket order.  A waiting worker adds one
+// to the team's `need`; a donor first claims part of `need` (an atomic subtraction), and
+// pushes only the records it claimed, so that the busy workers, who all see the same
+// waiting workers, do not all donate to them.  Slot p & qmask holds sequence p when free
+// for the producer of position p, and p + 1 once it holds that position's record.
 
-// Claims a slot; returns its position, or -1 when full/empty after bounded retries.
-__device__ __forceinline__ long long q_claim(uint32_t *ctr, const uint32_t *seq, uint32_t qmask,
-                                             bool push) {
-    uint32_t pos = ld_volatile(ctr);
+// Claims the tail position for a push; returns it, or -1 when the queue is full.
+__device__ __forceinline__ long long q_claim_tail(uint32_t *tail, const uint32_t *seq,
+                                                  uint32_t qmask) {
+    uint32_t pos = ld_volatile(tail);
     for (int it = 0; it < 256; ++it) {
-        const uint32_t s = ld_acquire(&seq[pos & qmask]);
-        const int dif = (int)(s - (push ? pos : pos + 1));
+        const int dif = (int)(ld_acquire(&seq[pos & qmask]) - pos);
         if (dif == 0) {
-            const uint32_t prev = atomicCAS(ctr, pos, pos + 1);
+            const uint32_t prev = atomicCAS(tail, pos, pos + 1);
             if (prev == pos) return (long long)pos;
             pos = prev;
         } else if (dif < 0) {
-            return -1;
+            return -1;                     // the consumer of the previous lap is still copying
         } else {
-            pos = ld_volatile(ctr);
+            pos = ld_volatile(tail);
         }
     }
     return -1;
@@ -71,7 +77,7 @@ static __device__ bool q_push(Team *T, uint32_t *seq, uint32_t *rec, int src_sm,
                        int R, int S, int W, bool override_rem, uint32_t my_rem) {
     const int lane = lane_id();
     long long pos = -1;
-    if (lane == 0) pos = q_claim(&T->tail, seq, (uint32_t)SA.qmask, true);
+    if (lane == 0) pos = q_claim_tail(&T->tail, seq, (uint32_t)SA.qmask);
     pos = __shfl_sync(FULLMASK, pos, 0);
     if (pos < 0) return false;
     uint32_t *dst = rec + (size_t)((uint32_t)pos & (uint32_t)SA.qmask) * SA.rmax;
@@ -85,25 +91,50 @@ static __device__ bool q_push(Team *T, uint32_t *seq, uint32_t *rec, int src_sm,
     return true;
 }
 
-// Pop a record into shared memory at `dst`.
-static __device__ bool q_pop(Team *T, uint32_t *seq, uint32_t *rec, int dst, int R) {
+// Receive the record of consumer ticket `t` into shared memory at `dst`, if it is there.
+static __device__ bool q_take(uint32_t *seq, uint32_t *rec, uint32_t t, int dst, int R) {
     const int lane = lane_id();
-    long long pos = -1;
-    if (lane == 0) pos = q_claim(&T->head, seq, (uint32_t)SA.qmask, false);
-    pos = __shfl_sync(FULLMASK, pos, 0);
-    if (pos < 0) return false;
-    const uint32_t slot = (uint32_t)pos & (uint32_t)SA.qmask;
+    const uint32_t slot = t & (uint32_t)SA.qmask;
+    int ready = 0;
+    if (lane == 0) ready = ld_acquire(&seq[slot]) == t + 1u;
+    if (!__shfl_sync(FULLMASK, ready, 0)) return false;
     __threadfence();
     copy_gs_cg(dst, rec + (size_t)slot * SA.rmax, R);
     __syncwarp();
     __threadfence();
-    if (lane == 0) st_release(&seq[slot], (uint32_t)pos + (uint32_t)SA.qmask + 1u);
+    if (lane == 0) st_release(&seq[slot], t + (uint32_t)SA.qmask + 1u);
     return true;
 }
 
+// longest back-off between two polls of an empty queue
+#ifndef CUBICS_POLL_MAX_NS
+#define CUBICS_POLL_MAX_NS 8192u
+#endif
+
+// nodes a worker explores in a record before it may donate from it
+#ifndef CUBICS_DONATE_AFTER
+#define CUBICS_DONATE_AFTER 0u
+#endif
+
+// a subtree of fewer nodes is small: not worth passing through the queue
+#ifndef CUBICS_SMALL_SUBTREE
+#define CUBICS_SMALL_SUBTREE 16ull
+#endif
+// records observed in a bin before its statistics are trusted
+#ifndef CUBICS_USTAT_MIN
+#define CUBICS_USTAT_MIN 8u
+#endif
+
+// most records one donation check may push
+#ifndef CUBICS_DONATE_MAX
+#define CUBICS_DONATE_MAX 16
+#endif
+
 // ------------------------------------------------------------------ worker
 
-template <int W, bool ST>
+// EXT: the worker can run the learned brancher and subtree logging.  Without them the
+// search compiles into a separate kernel that fits in fewer registers (more resident warps).
+template <int W, bool ST, bool EXT>
 struct Worker {
     IV<ST> I;
     Team *T;
@@ -112,6 +143,8 @@ struct Worker {
     int lsm, R, S;
     int top, base;        // open levels [0, top); levels >= base are in shared memory
     uint32_t tick;        // nodes of this worker (low bits pace the periodic checks)
+    int hungry;           // the last donation check saw workers waiting for records
+    uint32_t taken;       // tick when the current record was taken
     int gw;               // global worker index
     int team;             // batch: index of the team (its queue) being helped
     int inst;             // batch: instance being searched
@@ -223,8 +256,27 @@ struct Worker {
         __syncwarp();
     }
 
-    // donate the shallowest untried values when another worker is idle
-    __device__ void donate() {
+    // unfixed variables of the record at SM offset `Ls` (>= 0) or global `Lg` (every lane)
+    __device__ int count_unfixed(int Ls, const uint32_t *Lg) const {
+        int c = 0;
+        for (int v = lane_id(); v < I.n; v += 32) {
+            int p = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) p += __popc(Ls >= 0 ? SM[Ls + v * W + k] : Lg[v * W + k]);
+            c += p > 1;
+        }
+        return __reduce_add_sync(FULLMASK, c);
+    }
+    __device__ __forceinline__ int ubin(int u) const { return u * UBINS / (I.n + 1); }
+
+    // Donate to waiting workers, shallowest levels (the largest subtrees) first: claim up to
+    // `most` of the team's `need`, at most one per untried value of the level, and split the
+    // level's values one per record (the last record takes the rest), so that one donation
+    // feeds several waiting workers without records hopping from thief to thief.  The level
+    // being expanded keeps its lowest value.  A level is not given away when the records
+    // with its share of unfixed variables taken so far were mostly small subtrees; the
+    // levels below it are smaller still, so the donation ends there.
+    __device__ void donate(int most) {
         const int lane = lane_id();
         for (int s = 0; s < top; ++s) {
             const bool in_sm = s >= base;
@@ -232,27 +284,58 @@ struct Worker {
             const int Ls = in_sm ? slot(s) : -1;
             uint32_t r = 0u;
             if (lane < W) r = in_sm ? SM[Ls + S + lane] : Lg[S + lane];
-            const int pc = __reduce_add_sync(FULLMASK, __popc(r));
-            if (pc == 0) continue;
-            if (s == top - 1 && pc < 2) return;
-            // the top level keeps its lowest value; a deeper level gives all of them away
-            uint32_t give = r;
-            if (s == top - 1) {
+            int pc = __reduce_add_sync(FULLMASK, __popc(r));
+            if (s == top - 1) {                         // keep the lowest value
                 const uint32_t nz = __ballot_sync(FULLMASK, r != 0u);
-                if (lane == __ffs(nz) - 1) give = r & (r - 1);
+                if (nz && lane == __ffs(nz) - 1) r &= r - 1;
+                pc -= nz ? 1 : 0;
             }
-            if (lane == 0) atomicAdd(&T->work, 1);
-            if (q_push(T, qseq(), qrec(), Ls, Lg, R, S, W, true, give)) {
+            if (pc == 0) continue;
+            const int u = count_unfixed(Ls, Lg);
+            int worth = 1;
+            if (lane == 0) {
+                const unsigned long long st = ld_volatile(&T->ustat[ubin(u)]);
+                const uint32_t tot = (uint32_t)st, small = (uint32_t)(st >> 32);
+                worth = tot < CUBICS_USTAT_MIN || 2u * small <= tot;
+            }
+            if (!__shfl_sync(FULLMASK, worth, 0)) return;
+            int budget = 0;
+            if (lane == 0) {
+                const int k = min(most, pc);
+                const int prev = atomicSub(&T->need, k);
+                budget = min(max(prev, 0), k);
+                if (budget < k) atomicAdd(&T->need, k - budget);
+            }
+            budget = __shfl_sync(FULLMASK, budget, 0);
+            if (budget == 0) return;                      // nobody is waiting any more
+            most -= budget;
+            while (budget > 0) {
+                // give the highest value alone, or all that is left with the last record
+                uint32_t give = r;
+                if (budget > 1 && pc > 1) {
+                    const uint32_t nz = __ballot_sync(FULLMASK, r != 0u);
+                    const int k = 31 - __clz(nz);
+                    give = lane == k ? 1u << (31 - __clz(r)) : 0u;
+                }
+                if (lane == 0) atomicAdd(&T->work, 1);
+                if (!q_push(T, qseq(), qrec(), Ls, Lg, R, S, W, true, give)) {
+                    if (lane == 0) {                      // queue full: still owed
+                        atomicSub(&T->work, 1);
+                        atomicAdd(&T->need, budget);
+                    }
+                    return;
+                }
+                r &= ~give;
                 if (lane < W) {
-                    if (in_sm) SM[Ls + S + lane] = r & ~give;
-                    else Lg[S + lane] = r & ~give;
+                    if (in_sm) SM[Ls + S + lane] &= ~give;
+                    else Lg[S + lane] &= ~give;
                 }
                 __syncwarp();
                 if (lane == 0) ws().steals++;
-            } else if (lane == 0) {
-                atomicSub(&T->work, 1);
+                pc -= __reduce_add_sync(FULLMASK, __popc(give));
+                --budget;
             }
-            return;
+            if (most == 0) return;
         }
     }
 
@@ -397,12 +480,13 @@ struct Worker {
         tick++;
         // loads whose latency overlaps the fixpoint: stop flags and the donation signal
         const int p_stop = poll();
-        int p_idle = 0;
-        uint32_t p_qlen = 0;
-        const bool may_donate = !(SA.flags & F_NO_DONATE) && (tick & 7) == 0;
+        int p_need = 0;
+        // every 8th node; every node while workers are starved (ramp-up and the tail); never
+        // in the first nodes of a record, so that small subtrees are not passed on
+        const bool may_donate = !(SA.flags & F_NO_DONATE) && (hungry || (tick & 7) == 0) &&
+                                tick - taken >= CUBICS_DONATE_AFTER;
         if (may_donate && lane == 0) {
-            p_idle = ld_volatile(&T->idle);
-            p_qlen = ld_volatile(&T->tail) - ld_volatile(&T->head);
+            p_need = ld_volatile(&T->need);
         }
         if ((tick & 63) == 0) check_limits();
         unsigned long long ev = 0, rnd = 0;
@@ -429,8 +513,8 @@ struct Worker {
             refill();
             return;
         }
-        if (SA.mlp_off >= 0) y = select_learned(C, y);
-        if (SA.log_extra) {
+        if (EXT && SA.mlp_off >= 0) y = select_learned(C, y);
+        if (EXT && SA.log_extra) {
             // subtree logging: remember the node count and the chosen variable's features
             float f[N_FEATURES];
             const int nfixed = count_fixed_lane0(C);          // warp-wide reductions
@@ -464,8 +548,12 @@ struct Worker {
         __syncwarp();
         top = cl + 1;
         if (lane == 0 && top > ws().maxd) ws().maxd = top;
-        const int want = __shfl_sync(FULLMASK, (p_idle > 0 && (int)p_qlen < p_idle) ? 1 : 0, 0);
-        if (want) donate();
+        if (may_donate) {
+            // records owed to waiting workers, a bounded number per node
+            const int want = __shfl_sync(FULLMASK, min(p_need, CUBICS_DONATE_MAX), 0);
+            hungry = want > 0;
+            if (want > 0) donate(want);
+        }
     }
 
     // child of the top level: next value of its branching variable (the level is popped
@@ -477,7 +565,7 @@ struct Worker {
         const uint32_t r = lane < W ? SM[P + S + lane] : 0u;
         const uint32_t nz = __ballot_sync(FULLMASK, r != 0u);
         if (!nz) {
-            if (SA.log_extra) log_level(P);
+            if (EXT && SA.log_extra) log_level(P);
             top = p;
             refill();
             return;
@@ -488,7 +576,7 @@ struct Worker {
         const uint32_t rest = rw & (rw - 1);
         // the last value reuses the level's slot, unless the level must outlive its last
         // child to measure its subtree
-        const bool last = rest == 0u && (nz & ~(1u << k)) == 0u && !SA.log_extra;
+        const bool last = rest == 0u && (nz & ~(1u << k)) == 0u && !(EXT && SA.log_extra);
         const int x = (int)SM[P + S + W];
         int C, cl;
         __syncwarp();
@@ -530,14 +618,21 @@ struct Worker {
     __device__ void run() {
         const int lane = lane_id();
         for (;;) {
-            if (lane == 0) atomicAdd(&T->idle, 1);
+            uint32_t ticket = 0;
+            if (lane == 0) {
+                ticket = atomicAdd(&T->head, 1u);
+                atomicAdd(&T->need, 1);
+            }
+            ticket = __shfl_sync(FULLMASK, ticket, 0);
             const long long t0 = global_ns();
             int got = 0;
             unsigned sleep = 32;
-            for (;;) {
-                if (q_pop(T, qseq(), qrec(), slots, R)) { got = 1; break; }
+            for (int it = 0;; ++it) {
+                if (q_take(qseq(), qrec(), ticket, slots, R)) { got = 1; break; }
                 int done = 0;
-                if (lane == 0) {
+                if (lane == 0 && (it & 3) == 3) {   // termination and limits, every 4th poll
+                    // work == 0: no record is queued or being explored, so none will come;
+                    // the ticket is abandoned (the queue is not used again in this launch)
                     if (ld_volatile(&T->work) == 0 || ld_volatile(&SA.g->abort)) done = 1;
                     else if (global_ns() - t0 > SA.wait_limit_ns) {
                         atomicCAS(&SA.g->status, 0, CSP_ETIMEOUT_);
@@ -546,17 +641,20 @@ struct Worker {
                     }
                 }
                 if (__shfl_sync(FULLMASK, done, 0)) break;
-                __nanosleep(sleep);
-                sleep = sleep < 4096 ? sleep * 2 : 4096;
+                // jittered so that the waiting workers do not poll in step
+                __nanosleep(sleep + ((unsigned)gw * 97u & 511u));
+                sleep = sleep < CUBICS_POLL_MAX_NS ? sleep * 2 : CUBICS_POLL_MAX_NS;
             }
-            if (lane == 0) {
-                atomicSub(&T->idle, 1);
-                ws().wait_ns += global_ns() - t0;
-            }
+            if (lane == 0) ws().wait_ns += global_ns() - t0;
             if (!got) return;
+            taken = tick;
+            const int u = count_unfixed(slots, nullptr);
+            const unsigned long long n0 = ws().nodes;
             explore();
             __syncwarp();
             if (lane == 0) {
+                const bool small = ws().nodes - n0 < CUBICS_SMALL_SUBTREE;
+                atomicAdd(&T->ustat[ubin(u)], (small ? 1ull << 32 : 0ull) + 1ull);
                 __threadfence();
                 atomicSub(&T->work, 1);
             }
@@ -604,27 +702,26 @@ __device__ __forceinline__ void stage_instance(const uint32_t *ib) {
     for (int i = threadIdx.x; i < words / 4; i += blockDim.x) d[i] = s[i];
 }
 
-template <int W, bool ST>
-#ifndef CUBICS_SEARCH_MINB
-#define CUBICS_SEARCH_MINB 1
-#endif
-__global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const SearchArgs Ap) {
+template <int W, bool ST, bool EXT>
+__device__ __forceinline__ void search_body(const SearchArgs &Ap) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     __shared__ int s_inst, s_team;
     if (threadIdx.x == 0) SA = Ap;
     __syncthreads();
     const int per_warp = SA.lsm * SA.rmax + WS_WORDS + SA.feat_words + SA.list_words;
-    if (SA.mlp_off >= 0) {           // the brancher's weights, staged once per block
+    if (EXT && SA.mlp_off >= 0) {    // the brancher's weights, staged once per block
         for (int i = threadIdx.x; i < PK_WORDS; i += blockDim.x) SM[SA.mlp_off + i] = __ldg(SA.mlp + i);
         __syncthreads();
     }
 
-    Worker<W, ST> wk;
+    Worker<W, ST, EXT> wk;
     wk.lsm = SA.lsm;
     wk.slots = SA.warp_base + warp * per_warp;
     wk.wso = wk.slots + SA.lsm * SA.rmax;
     wk.gw = blockIdx.x * SA.warps + warp;
     wk.tick = 0;
+    wk.hungry = 1;                   // the first nodes feed the idle workers at once
+    wk.taken = 0;
     wk.stop = 0;
     wk.team = 0;
     wk.inst = 0;
@@ -694,6 +791,11 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
             for (int k = lane; k < wk.R; k += 32)
                 SM[wk.slots + k] = k < wk.S ? root[k] : (k == wk.S + W ? 0xffffffffu : 0u);
             if (lane == 0) {
+                // the block's workers abandoned their tickets when the previous instance
+                // ended; no other block uses this queue before work is set
+                T->head = ld_volatile(&T->tail);
+                T->need = 0;
+                for (int b = 0; b < UBINS; ++b) T->ustat[b] = 0ull;
                 T->inst = i;
                 T->found = 0;
                 T->progress = 0;
@@ -729,6 +831,28 @@ __global__ void __launch_bounds__(512, CUBICS_SEARCH_MINB) search_kernel(const S
     wk.flush();
 }
 
+// Register caps of the plain search kernel (first-fail, no logging), the lowest at which it
+// compiles without spills for its staged form: 80 registers for one-word domains (24
+// resident warps per SM), 96 for wider ones (20).
+#ifndef CUBICS_REGS_W1
+#define CUBICS_REGS_W1 80
+#endif
+#ifndef CUBICS_REGS_WN
+#define CUBICS_REGS_WN 96
+#endif
+
+template <int W, bool ST>
+__global__ void __maxnreg__(W == 1 ? CUBICS_REGS_W1 : CUBICS_REGS_WN)
+    search_kernel(const SearchArgs Ap) {
+    search_body<W, ST, false>(Ap);
+}
+
+// learned brancher and/or subtree logging
+template <int W, bool ST>
+__global__ void __launch_bounds__(512, 1) search_kernel_ext(const SearchArgs Ap) {
+    search_body<W, ST, true>(Ap);
+}
+
 // ------------------------------------------------------------------ propagate kernel
 
 template <int W, bool ST>
@@ -759,22 +883,40 @@ __global__ void __launch_bounds__(256) propagate_kernel(PropArgs P) {
 
 // ------------------------------------------------------------------ host launchers
 
-template <int W, bool ST>
-cudaError_t launch_search_t(const SearchArgs &A, int blocks, int threads, size_t smem,
-                            cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<W, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename K>
+cudaError_t launch_k(K kern, const SearchArgs &A, int blocks, int threads, size_t smem,
+                     cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    search_kernel<W, ST><<<blocks, threads, smem, st>>>(A);
+    kern<<<blocks, threads, smem, st>>>(A);
     return cudaGetLastError();
 }
 
-template <int W, bool ST>
-cudaError_t occupancy_t(int threads, size_t smem, int *bps) {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<W, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename K>
+cudaError_t occupancy_k(K kern, int threads, size_t smem, int *bps) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, search_kernel<W, ST>, threads, smem);
+    if (threads > fa.maxThreadsPerBlock) {   // the register cap admits no block this large
+        *bps = 0;
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, threads, smem);
+}
+
+template <int W, bool ST, bool EXT>
+cudaError_t launch_search_t(const SearchArgs &A, int blocks, int threads, size_t smem,
+                            cudaStream_t st) {
+    if constexpr (EXT) return launch_k(search_kernel_ext<W, ST>, A, blocks, threads, smem, st);
+    else return launch_k(search_kernel<W, ST>, A, blocks, threads, smem, st);
+}
+
+template <int W, bool ST, bool EXT>
+cudaError_t occupancy_t(int threads, size_t smem, int *bps) {
+    if constexpr (EXT) return occupancy_k(search_kernel_ext<W, ST>, threads, smem, bps);
+    else return occupancy_k(search_kernel<W, ST>, threads, smem, bps);
 }
 
 template <int W, bool ST>
@@ -786,20 +928,28 @@ cudaError_t launch_prop_t(const PropArgs &P, int blocks, int threads, size_t sme
     return cudaGetLastError();
 }
 
-// one translation unit per W defines these for both staging modes
+// Two translation units per W (so that they compile in parallel): one defines the plain
+// search kernels and the propagate kernels, the other the search kernels with the learned
+// brancher and logging; each for both staging modes.
+#define CUBICS_DEFINE_SEARCH(WW, EXT, SFX)                                                   \
+    cudaError_t launch_search##SFX##_w##WW(bool st_, const SearchArgs &A, int b, int t,     \
+                                           size_t sm, cudaStream_t s) {                     \
+        return st_ ? launch_search_t<WW, true, EXT>(A, b, t, sm, s)                         \
+                   : launch_search_t<WW, false, EXT>(A, b, t, sm, s);                       \
+    }                                                                                       \
+    cudaError_t occupancy##SFX##_w##WW(bool st_, int t, size_t sm, int *bps) {              \
+        return st_ ? occupancy_t<WW, true, EXT>(t, sm, bps)                                 \
+                   : occupancy_t<WW, false, EXT>(t, sm, bps);                               \
+    }
+
 #define CUBICS_DEFINE_WIDTH(WW)                                                              \
-    cudaError_t launch_search_w##WW(bool st_, const SearchArgs &A, int b, int t, size_t sm, \
-                                    cudaStream_t s) {                                       \
-        return st_ ? launch_search_t<WW, true>(A, b, t, sm, s)                              \
-                   : launch_search_t<WW, false>(A, b, t, sm, s);                            \
-    }                                                                                       \
-    cudaError_t occupancy_w##WW(bool st_, int t, size_t sm, int *bps) {                     \
-        return st_ ? occupancy_t<WW, true>(t, sm, bps) : occupancy_t<WW, false>(t, sm, bps); \
-    }                                                                                       \
+    CUBICS_DEFINE_SEARCH(WW, false, )                                                        \
     cudaError_t launch_prop_w##WW(bool st_, const PropArgs &P, int b, int t, size_t sm,     \
                                   cudaStream_t s) {                                         \
         return st_ ? launch_prop_t<WW, true>(P, b, t, sm, s)                                \
                    : launch_prop_t<WW, false>(P, b, t, sm, s);                              \
     }
+
+#define CUBICS_DEFINE_WIDTH_EXT(WW) CUBICS_DEFINE_SEARCH(WW, true, _ext)
 
 }  // namespace cubics

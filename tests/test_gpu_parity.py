@@ -301,6 +301,19 @@ def test_small_workspace_is_enomem():
     assert L.csp_solve(p.h, K.CSP_ALL, 0, sols.ctypes.data_as(K._I32P), None) == K.CSP_ENOMEM
 
 
+def test_block_beyond_register_budget_is_einval():
+    # the first-fail kernel is capped below 64 K / 1024 registers per thread: a 32-warp block
+    # does not fit, a 16-warp block does
+    p = K.Csp(I.queens(8))
+    p.set_tiling(K.tiling(warps_per_block=32))
+    with pytest.raises(K.CspError) as e:
+        p.workspace_bytes(K.CSP_ALL, 0)
+    assert e.value.code == K.CSP_EINVAL
+    p.set_tiling(K.tiling(warps_per_block=16))
+    rc, st, _ = p.solve(K.CSP_ALL, 0)
+    assert rc == 0 and st["solutions"] == queens_count(8)
+
+
 # ----------------------------------------------------------------------------- batches
 
 def _rb_small(count, first=0):
