@@ -64,14 +64,18 @@ struct Team {                 // one work-sharing group (whole grid or one block
     int32_t pad2[31];
     uint32_t tail;            // producer positions (own 128-byte line)
     int32_t pad3[31];
-    int32_t need;             // waiting workers not yet promised a record (own line)
+    uint32_t promised;        // records pushed or promised by donors (own line); head -
+                              // promised > 0: workers wait for records nobody has promised
     int32_t pad4[31];
-    // sizes of the subtrees taken from the queue, by the share of unfixed variables in the
-    // record (bin u * UBINS / (n + 1)): low 32 bits count them, high 32 bits count the small ones
-    unsigned long long ustat[32];
+    // subtrees taken from the queue, by the share of unfixed variables in the record (bin
+    // u * UBINS / (n + 1)): how many, and their nodes in total
+    uint32_t ucnt[32];
+    unsigned long long usum[32];
+    unsigned long long xns, xnodes;   // time and nodes spent in finished records
+    int32_t pad5[28];
 };
 constexpr int UBINS = 32;
-static_assert(sizeof(Team) == 768, "Team is six 128-byte lines");
+static_assert(sizeof(Team) == 1024, "Team is eight 128-byte lines");
 
 struct GState {               // counters of one launch
     unsigned long long nodes, fails, solutions, hsum, hxor, evals, steals, spills;

@@ -76,6 +76,7 @@ __global__ void init_single_kernel(SearchArgs A) {
         if (threadIdx.x == 0) {
             A.teams[0].work = 1;
             A.teams[0].tail = 1;
+            A.teams[0].promised = 1;
         }
     }
 }

@@ -46,11 +46,11 @@ static_assert(sizeof(WarpShared) == 4 * WS_WORDS, "WarpShared size must match WS
 // a compare-and-swap on the tail (a full queue makes the push fail, and the donor keeps its
 // values).  Consumers take a ticket with a fetch-and-add on the head, which never fails,
 // and wait for their own slot to be filled: waiting workers poll distinct words instead of
-// all racing for the head, and they are served in ticket order.  A waiting worker adds one
-// to the team's `need`; a donor first claims part of `need` (an atomic subtraction), and
-// pushes only the records it claimed, so that the busy workers, who all see the same
-// waiting workers, do not all donate to them.  Slot p & qmask holds sequence p when free
-// for the producer of position p, and p + 1 once it holds that position's record.
+// all racing for the head, and they are served in ticket order.  Donors count the records
+// they will push in the team's `promised` (an atomic addition before the push), and give
+// only while head - promised > 0, so that the busy workers, who all see the same waiting
+// workers, do not all donate to them.  Slot p & qmask holds sequence p when free for the
+// producer of position p, and p + 1 once it holds that position's record.
 
 // Claims the tail position for a push; returns it, or -1 when the queue is full.
 __device__ __forceinline__ long long q_claim_tail(uint32_t *tail, const uint32_t *seq,
@@ -116,9 +116,14 @@ static __device__ bool q_take(uint32_t *seq, uint32_t *rec, uint32_t t, int dst,
 #define CUBICS_DONATE_AFTER 0u
 #endif
 
-// a subtree of fewer nodes is small: not worth passing through the queue
-#ifndef CUBICS_SMALL_SUBTREE
-#define CUBICS_SMALL_SUBTREE 16ull
+// Records whose subtrees took less time on average (ns) are not worth passing through the
+// queue: the donor's push and the taker's copy cost more than they spread.  The whole grid
+// sharing one queue (single problem) pays more per record than a block's queue (batch).
+#ifndef CUBICS_SMALL_NS_GRID
+#define CUBICS_SMALL_NS_GRID 80000.f
+#endif
+#ifndef CUBICS_SMALL_NS_BATCH
+#define CUBICS_SMALL_NS_BATCH 30000.f
 #endif
 // records observed in a bin before its statistics are trusted
 #ifndef CUBICS_USTAT_MIN
@@ -145,6 +150,8 @@ struct Worker {
     uint32_t tick;        // nodes of this worker (low bits pace the periodic checks)
     int hungry;           // the last donation check saw workers waiting for records
     uint32_t taken;       // tick when the current record was taken
+    int pbin;             // size-statistics bin of the current record
+    uint32_t credited;    // tick up to which its nodes were added to the bin
     int gw;               // global worker index
     int team;             // batch: index of the team (its queue) being helped
     int inst;             // batch: instance being searched
@@ -201,6 +208,8 @@ struct Worker {
     // the team's instance stops (found = 2) and the others go on.
     __device__ void check_limits() {
         if (lane_id() == 0) {
+            atomicAdd(&T->usum[pbin], (unsigned long long)(tick - credited));
+            credited = tick;
             if (SA.node_limit > 0 && SA.batch) {
                 const unsigned long long tot = atomicAdd(&T->progress, 64ull) + 64ull;
                 if ((long long)tot >= SA.node_limit) atomicCAS(&T->found, 0, 2);
@@ -269,12 +278,12 @@ struct Worker {
     }
     __device__ __forceinline__ int ubin(int u) const { return u * UBINS / (I.n + 1); }
 
-    // Donate to waiting workers, shallowest levels (the largest subtrees) first: claim up to
-    // `most` of the team's `need`, at most one per untried value of the level, and split the
+    // Donate to waiting workers, shallowest levels (the largest subtrees) first: promise up
+    // to `most` records owed to them, at most one per untried value of the level, split the
     // level's values one per record (the last record takes the rest), so that one donation
     // feeds several waiting workers without records hopping from thief to thief.  The level
     // being expanded keeps its lowest value.  A level is not given away when the records
-    // with its share of unfixed variables taken so far were mostly small subtrees; the
+    // with its share of unfixed variables taken so far took little time on average; the
     // levels below it are smaller still, so the donation ends there.
     __device__ void donate(int most) {
         const int lane = lane_id();
@@ -294,17 +303,25 @@ struct Worker {
             const int u = count_unfixed(Ls, Lg);
             int worth = 1;
             if (lane == 0) {
-                const unsigned long long st = ld_volatile(&T->ustat[ubin(u)]);
-                const uint32_t tot = (uint32_t)st, small = (uint32_t)(st >> 32);
-                worth = tot < CUBICS_USTAT_MIN || 2u * small <= tot;
+                // average time of a record from this bin: its mean nodes times the team's
+                // mean time per node (nodes differ in cost from one problem to another)
+                const uint32_t cnt = ld_volatile(&T->ucnt[ubin(u)]);
+                const unsigned long long xn = ld_volatile(&T->xnodes);
+                if (cnt >= CUBICS_USTAT_MIN && xn > 0) {
+                    const float mean_nodes = (float)ld_volatile(&T->usum[ubin(u)]) / (float)cnt;
+                    const float node_ns = (float)ld_volatile(&T->xns) / (float)xn;
+                    worth = mean_nodes * node_ns >=
+                            (SA.batch ? CUBICS_SMALL_NS_BATCH : CUBICS_SMALL_NS_GRID);
+                }
             }
             if (!__shfl_sync(FULLMASK, worth, 0)) return;
             int budget = 0;
             if (lane == 0) {
                 const int k = min(most, pc);
-                const int prev = atomicSub(&T->need, k);
-                budget = min(max(prev, 0), k);
-                if (budget < k) atomicAdd(&T->need, k - budget);
+                const uint32_t h = ld_volatile(&T->head);
+                const uint32_t p0 = atomicAdd(&T->promised, (uint32_t)k);
+                budget = min(max((int)(h - p0), 0), k);
+                if (budget < k) atomicSub(&T->promised, (uint32_t)(k - budget));
             }
             budget = __shfl_sync(FULLMASK, budget, 0);
             if (budget == 0) return;                      // nobody is waiting any more
@@ -319,9 +336,9 @@ struct Worker {
                 }
                 if (lane == 0) atomicAdd(&T->work, 1);
                 if (!q_push(T, qseq(), qrec(), Ls, Lg, R, S, W, true, give)) {
-                    if (lane == 0) {                      // queue full: still owed
+                    if (lane == 0) {                      // queue full: not given
                         atomicSub(&T->work, 1);
-                        atomicAdd(&T->need, budget);
+                        atomicSub(&T->promised, (uint32_t)budget);
                     }
                     return;
                 }
@@ -480,13 +497,14 @@ struct Worker {
         tick++;
         // loads whose latency overlaps the fixpoint: stop flags and the donation signal
         const int p_stop = poll();
-        int p_need = 0;
+        uint32_t p_head = 0, p_prom = 0;
         // every 8th node; every node while workers are starved (ramp-up and the tail); never
         // in the first nodes of a record, so that small subtrees are not passed on
         const bool may_donate = !(SA.flags & F_NO_DONATE) && (hungry || (tick & 7) == 0) &&
                                 tick - taken >= CUBICS_DONATE_AFTER;
         if (may_donate && lane == 0) {
-            p_need = ld_volatile(&T->need);
+            p_head = ld_volatile(&T->head);
+            p_prom = ld_volatile(&T->promised);
         }
         if ((tick & 63) == 0) check_limits();
         unsigned long long ev = 0, rnd = 0;
@@ -550,7 +568,8 @@ struct Worker {
         if (lane == 0 && top > ws().maxd) ws().maxd = top;
         if (may_donate) {
             // records owed to waiting workers, a bounded number per node
-            const int want = __shfl_sync(FULLMASK, min(p_need, CUBICS_DONATE_MAX), 0);
+            const int owed = max((int)(p_head - p_prom), 0);
+            const int want = __shfl_sync(FULLMASK, min(owed, CUBICS_DONATE_MAX), 0);
             hungry = want > 0;
             if (want > 0) donate(want);
         }
@@ -619,10 +638,7 @@ struct Worker {
         const int lane = lane_id();
         for (;;) {
             uint32_t ticket = 0;
-            if (lane == 0) {
-                ticket = atomicAdd(&T->head, 1u);
-                atomicAdd(&T->need, 1);
-            }
+            if (lane == 0) ticket = atomicAdd(&T->head, 1u);
             ticket = __shfl_sync(FULLMASK, ticket, 0);
             const long long t0 = global_ns();
             int got = 0;
@@ -648,13 +664,19 @@ struct Worker {
             if (lane == 0) ws().wait_ns += global_ns() - t0;
             if (!got) return;
             taken = tick;
-            const int u = count_unfixed(slots, nullptr);
-            const unsigned long long n0 = ws().nodes;
+            // the record counts in its bin now; its nodes are credited as they are explored
+            // (every 64th node and at the end), so that a large subtree still running
+            // already raises its bin's average
+            pbin = ubin(count_unfixed(slots, nullptr));
+            credited = tick;
+            const long long t_taken = global_ns();
+            if (lane == 0) atomicAdd(&T->ucnt[pbin], 1u);
             explore();
             __syncwarp();
             if (lane == 0) {
-                const bool small = ws().nodes - n0 < CUBICS_SMALL_SUBTREE;
-                atomicAdd(&T->ustat[ubin(u)], (small ? 1ull << 32 : 0ull) + 1ull);
+                atomicAdd(&T->usum[pbin], (unsigned long long)(tick - credited));
+                atomicAdd(&T->xnodes, (unsigned long long)(tick - taken));
+                atomicAdd(&T->xns, (unsigned long long)(global_ns() - t_taken));
                 __threadfence();
                 atomicSub(&T->work, 1);
             }
@@ -722,6 +744,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
     wk.tick = 0;
     wk.hungry = 1;                   // the first nodes feed the idle workers at once
     wk.taken = 0;
+    wk.pbin = 0;
+    wk.credited = 0;
     wk.stop = 0;
     wk.team = 0;
     wk.inst = 0;
@@ -793,9 +817,14 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
             if (lane == 0) {
                 // the block's workers abandoned their tickets when the previous instance
                 // ended; no other block uses this queue before work is set
-                T->head = ld_volatile(&T->tail);
-                T->need = 0;
-                for (int b = 0; b < UBINS; ++b) T->ustat[b] = 0ull;
+                const uint32_t t = ld_volatile(&T->tail);
+                T->head = t;
+                T->promised = t + 1u;                       // the root record, pushed below
+                for (int b = 0; b < UBINS; ++b) {
+                    T->ucnt[b] = 0u;
+                    T->usum[b] = 0ull;
+                }
+                T->xns = T->xnodes = 0ull;
                 T->inst = i;
                 T->found = 0;
                 T->progress = 0;
