@@ -488,6 +488,142 @@ class LinAdBatch(RBBatch):
         return self._oracle_instances(0, 1.5)
 
 
+class LNSRound(RBBatch):
+    """Parallel large neighbourhood search on a mixed instance (200 vars on 0..255, 60 rows,
+    20 alldifferent groups) with objective min sum w_i x_i, w_i ~ U[1, 9]: one step is one
+    search round, 256 neighbourhoods (about 10 % of the variables reset, the others fixed to
+    the incumbent, objective <= incumbent - 1) in one launch, first solution each."""
+
+    COPIES, FRAC, NODE_LIMIT, WARM_ROUNDS = 256, 0.1, 5000, 3
+
+    def __init__(self):
+        from paper_1909_09213_gb300 import instances as I
+        self.model = I.lin_alldiff(I.seed_for(I.CFG_LINAD, 0))
+        self.obj = I.objective_weights(0, self.model.n)
+        self.count = self.COPIES
+        self.desc = (f"LNS round on a mixed instance (200 vars on 0..255, 60 int_lin_le rows, 20 "
+                     f"alldifferent groups of 10), objective min sum w_i x_i (w ~ U[1,9]): "
+                     f"{self.COPIES} neighbourhoods, {self.FRAC:.0%} of the vars reset, "
+                     f"{self.NODE_LIMIT} nodes at most each, first solution, one launch (CUDA graph)")
+        self.profile = "search_kernel_lns_linad.md"
+
+    def golden(self):
+        return None
+
+    def bytes_per_node(self):
+        """2 n W 4 + the oracle's wake bytes, from first-solution searches of 4 neighbourhoods
+        of the round (500 nodes at most each)"""
+        from oracle import lns_ref as L
+        from oracle import oracle as O
+        nodes, by = 0, 0.0
+        for mk in self.masks[:4]:
+            m = L.neighbourhood_model(self.model, self.inc, mk, self.obj, self.bound)
+            r = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1, W=8, node_limit=500)
+            nodes += r.nodes
+            by += r.work_bytes + r.nodes * 2 * m.n * 8 * 4
+        return by / max(nodes, 1)
+
+    def setup(self, K, stream):
+        from paper_1909_09213_gb300 import instances as I
+        from paper_1909_09213_gb300 import lns
+        self.lns_mod = lns
+        # a mid-search incumbent: the first solution, improved by a few rounds (untimed)
+        self.search = lns.LNS(self.model, self.obj, copies=self.COPIES, frac=self.FRAC,
+                              node_limit=self.NODE_LIMIT, seed=1)
+        self.initial_value = self.search.initial()
+        for r in range(self.WARM_ROUNDS):
+            self.search.round(r)
+        self.inc = self.search.incumbent.copy()
+        self.value = self.search.value
+        self.bound = self.value - 1
+        self.masks = I.relax_masks(self.model.n, self.COPIES, self.FRAC, 1000, 1)
+        self.probs = [lns.neighbourhood(self.search.base, self.inc, mk, self.obj, self.bound)
+                      for mk in self.masks]
+        self.tiling = K.tiling(warps_per_block=4, smem_levels=4)
+        self.tune_entry = {"calib": None}
+        self.lim = K.limits(node_limit=self.NODE_LIMIT)
+        self.b = K.Batch(self.probs)
+        self.b.stream = stream
+        self.b.set_tiling(self.tiling)
+        self.b.bind(K.CSP_FIRST, stream)
+        self.rc, self.res = self.b.solve(K.CSP_FIRST, lim=self.lim, use_graph=True, bind=False)
+
+    def launch(self, K):
+        import ctypes
+        K._check(K.lib().csp_batch_launch(self.b.b, ctypes.byref(self.lim), 1), "csp_batch_launch")
+
+    def e2e_step(self, K):
+        rc, res = self.b.solve(K.CSP_FIRST, lim=self.lim, use_graph=True, bind=False)
+        st = self.b.stats()
+        st["nodes"] = sum(r["nodes"] for r in res)
+        st["h2d_bytes"] = 0
+        st["d2h_bytes"] = self.count * 40 + 4 * K.lib().csp_batch_solution_words(self.b.b)
+        return st
+
+    def parity(self, st):
+        # every solution satisfies the model, the fixings and the bound; the verdicts of the
+        # first 8 neighbourhoods equal the oracle's where it decides them within 5 000 nodes
+        from oracle import lns_ref as L
+        from oracle import oracle as O
+        om = O.OracleModel(self.model)
+        ok = True
+        for mk, r in zip(self.masks, self.res):
+            if r["status"] == 1:
+                s = self.sol[r["sol_offset"]:r["sol_offset"] + r["n"]]
+                ok &= O.check_solution(om, s) and L.objective(self.obj, s) <= self.bound
+                ok &= all(s[x] == self.inc[x] for x in range(self.model.n) if not mk[x])
+        for mk, r in list(zip(self.masks, self.res))[:8]:
+            want = L.verdict(L.neighbourhood_model(self.model, self.inc, mk, self.obj, self.bound),
+                             node_limit=5_000)
+            if want >= 0 and r["status"] >= 0:
+                ok &= want == r["status"]
+        return ok
+
+    def extra(self, K, st):
+        sat = sum(r["status"] == 1 for r in self.res)
+        unsat = sum(r["status"] == 0 for r in self.res)
+        # the whole search from scratch, 20 s at most (untimed by the events; wall clock)
+        note("full LNS run")
+        res = self.lns_mod.LNS(self.model, self.obj, copies=self.COPIES, frac=self.FRAC,
+                               node_limit=self.NODE_LIMIT, seed=2).run(rounds=200, time_budget_s=20)
+        return {"copies": self.count, "sat": sat, "unsat": unsat,
+                "undecided_at_node_limit": self.count - sat - unsat,
+                "incumbent_of_the_timed_round": int(self.value),
+                "full_search": {"initial": res.initial, "best": res.best, "optimal": res.optimal,
+                                "rounds": len(res.rounds), "nodes": res.nodes,
+                                "kernel_ms": res.kernel_ms, "wall_ms": res.wall_ms,
+                                "trajectory": [(r.round, r.best, round(r.wall_ms, 1))
+                                               for r in res.rounds if r.improved]}}
+
+    def _oracle_copies(self, budget_s, node_limit=20_000):
+        from oracle import lns_ref as L
+        from oracle import oracle as O
+        if not hasattr(self, "inc"):
+            # the reference arm has no GPU incumbent: the oracle's first solution instead
+            from paper_1909_09213_gb300 import instances as I
+            r = O.solve(O.OracleModel(self.model), mode=1, cap=1, variant=1)
+            self.inc = r.sols[0].copy()
+            self.value = L.objective(self.obj, self.inc)
+            self.bound = self.value - 1
+            self.masks = I.relax_masks(self.model.n, self.COPIES, self.FRAC, 1000, 1)
+        nodes, secs, k = 0, 0.0, 0
+        while secs < budget_s and k < len(self.masks):
+            m = L.neighbourhood_model(self.model, self.inc, self.masks[k], self.obj, self.bound)
+            t = time.perf_counter()
+            r = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1, node_limit=node_limit)
+            secs += time.perf_counter() - t
+            nodes += r.nodes
+            k += 1
+        return nodes, secs, (f"neighbourhoods 0..{k - 1} of the round, first solution each "
+                             f"(at most {node_limit} nodes each)")
+
+    def cpu_sample(self):
+        return self._oracle_copies(12.0)
+
+    def reference_step(self):
+        return self._oracle_copies(1.5)
+
+
 def make_workload(name):
     if name == "queens16":
         return Queens(16)
@@ -499,6 +635,8 @@ def make_workload(name):
         return LinAdBatch(256)
     if name == "rb_learned":
         return LearnedRB()
+    if name == "lns":
+        return LNSRound()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -638,7 +776,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="queens16",
-                    choices=["queens16", "queens14", "rb4096", "rb_learned", "linad256"])
+                    choices=["queens16", "queens14", "rb4096", "rb_learned", "linad256", "lns"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

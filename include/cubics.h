@@ -136,6 +136,21 @@ int csp_post_table(csp_t *h, int32_t x, int32_t y, const uint32_t *allowed, int3
 /* Device domain layout: n variables, W uint32 words per domain, bit k = value lo0 + k. */
 int csp_layout(const csp_t *h, int32_t *n, int32_t *W, int32_t *lo0);
 
+/* Root domains as the kernels receive them: `host_out` gets n * W words in the layout of
+ * csp_layout.  Host only (no device needed).  CSP_EINVAL for NULL arguments. */
+int csp_root_domains(const csp_t *h, uint32_t *host_out);
+
+/* A new handle holding a copy of the model of `src` (variables, domains, constraints,
+ * tiling, brancher and its weights, partition); it is unbound and independent of `src`.
+ * The paper has no counterpart: large neighbourhood search (Section 4, first direction)
+ * builds each neighbourhood as a copy of the problem with some domains reset.  Host only. */
+int csp_clone(const csp_t *src, csp_t **out);
+
+/* Restrict D_{vars[t]} to {values[t]} for t < count (the domain becomes empty when the value
+ * is not in it).  vars, values: host arrays of count entries.  CSP_EINVAL for a bad index
+ * (nothing is changed then).  Host only. */
+int csp_fix_values(csp_t *h, int32_t count, const int32_t *vars, const int32_t *values);
+
 /* ---------------------------------------------------------------- device (single problem) */
 
 /* Launch shape; NULL or zero fields restore the library's choice.  Changes the workspace

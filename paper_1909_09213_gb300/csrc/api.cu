@@ -562,6 +562,59 @@ int csp_post_table(csp_t *h, int32_t x, int32_t y, const uint32_t *allowed, int3
     return CSP_OK;
 }
 
+int csp_root_domains(const csp_t *h, uint32_t *out) {
+    if (!h || !out) return CSP_EINVAL;
+    const int W = h->W;
+    for (int i = 0; i < h->n; ++i) {
+        for (int k = 0; k < W; ++k) out[(size_t)i * W + k] = 0u;
+        for (int32_t v = h->lo[i]; v <= h->hi[i]; ++v) {
+            if (!h->present[i][v - h->lo[i]]) continue;
+            const int b = v - h->lo0;
+            out[(size_t)i * W + b / 32] |= 1u << (b % 32);
+        }
+    }
+    return CSP_OK;
+}
+
+int csp_clone(const csp_t *src, csp_t **out) {
+    if (!src || !out) return CSP_EINVAL;
+    csp *h = new csp();
+    h->n = src->n;
+    h->lo = src->lo;
+    h->hi = src->hi;
+    h->present = src->present;
+    h->ne_x = src->ne_x;
+    h->ne_y = src->ne_y;
+    h->ne_c = src->ne_c;
+    h->lin = src->lin;
+    h->ad = src->ad;
+    h->tab = src->tab;
+    h->lo0 = src->lo0;
+    h->W = src->W;
+    h->tiling = src->tiling;
+    h->brancher = src->brancher;
+    h->mlp_params = src->mlp_params;
+    h->part = src->part;
+    h->nparts = src->nparts;
+    *out = h;
+    return CSP_OK;
+}
+
+int csp_fix_values(csp_t *h, int32_t count, const int32_t *vars, const int32_t *values) {
+    if (!h || count < 0 || (count > 0 && (!vars || !values))) return CSP_EINVAL;
+    for (int t = 0; t < count; ++t)
+        if (!var_ok(h, vars[t])) return CSP_EINVAL;
+    for (int t = 0; t < count; ++t) {
+        const int32_t v = vars[t], val = values[t];
+        std::vector<uint8_t> &p = h->present[v];
+        const bool had = val >= h->lo[v] && val <= h->hi[v] && p[val - h->lo[v]];
+        std::fill(p.begin(), p.end(), (uint8_t)0);
+        if (had) p[val - h->lo[v]] = 1;
+    }
+    invalidate(h);
+    return CSP_OK;
+}
+
 int csp_layout(const csp_t *h, int32_t *n, int32_t *W, int32_t *lo0) {
     if (!h) return CSP_EINVAL;
     if (n) *n = h->n;

@@ -61,6 +61,9 @@ SIGNATURES = {
     "csp_post_alldiff": (C.c_int, [_VP, C.c_int32, _I32P]),
     "csp_post_table": (C.c_int, [_VP, C.c_int32, C.c_int32, _U32P, C.c_int32]),
     "csp_layout": (C.c_int, [_VP, _I32P, _I32P, _I32P]),
+    "csp_root_domains": (C.c_int, [_VP, _U32P]),
+    "csp_clone": (C.c_int, [_VP, C.POINTER(_VP)]),
+    "csp_fix_values": (C.c_int, [_VP, C.c_int32, _I32P, _I32P]),
     "csp_set_tiling": (C.c_int, [_VP, C.POINTER(csp_tiling)]),
     "csp_workspace_bytes": (C.c_int, [_VP, C.c_int32, C.c_int64, C.POINTER(C.c_size_t)]),
     "csp_bind": (C.c_int, [_VP, _VP, C.c_size_t, _VP]),
@@ -201,6 +204,33 @@ class Csp:
         if h is not None and _lib is not None:
             _lib.csp_destroy(h)
             self.h = None
+
+    def clone(self) -> "Csp":
+        """csp_clone: an unbound copy of this problem (its model object is shared)."""
+        h = _VP()
+        _check(lib().csp_clone(self.h, C.byref(h)), "csp_clone")
+        c = object.__new__(Csp)
+        c.model, c.h, c.ws, c.stream = self.model, h, None, None
+        return c
+
+    def fix_values(self, vars_, values):
+        """csp_fix_values: D(vars_[t]) := D(vars_[t]) & {values[t]}."""
+        v, a = _i32(vars_), _i32(values)
+        _check(lib().csp_fix_values(self.h, len(v), _ptr(v, _I32P), _ptr(a, _I32P)),
+               "csp_fix_values")
+
+    def post_lin(self, coefs, vars_, rhs: int):
+        """csp_post_int_lin_le on this handle."""
+        a, v = _i32(coefs), _i32(vars_)
+        _check(lib().csp_post_int_lin_le(self.h, len(a), _ptr(a, _I32P), _ptr(v, _I32P), int(rhs)),
+               "csp_post_int_lin_le")
+
+    def root_domains(self) -> np.ndarray:
+        """csp_root_domains: (n, W) uint32 words in the layout of csp_layout."""
+        n, W, _ = self.layout()
+        out = np.zeros(n * W, dtype=np.uint32)
+        _check(lib().csp_root_domains(self.h, _ptr(out, _U32P)), "csp_root_domains")
+        return out.reshape(n, W)
 
     def layout(self):
         n, W, lo0 = C.c_int32(), C.c_int32(), C.c_int32()

@@ -30,6 +30,7 @@ BASE_SEED = 20190920
 
 # config identifiers used to derive per-instance seeds
 CFG_QUEENS, CFG_RB, CFG_RB_TRAIN, CFG_RB_EVAL, CFG_LINAD, CFG_TINY = 1, 3, 40, 41, 5, 99
+CFG_LNS_OBJ, CFG_LNS_RELAX = 60, 61     # objective weights; neighbourhood draws
 
 
 def _mix64(z: int) -> int:
@@ -266,3 +267,35 @@ def random_tiny(seed: int, n_max: int = 6, d_max: int = 5, kinds=("ne", "lin", "
             allowed = (s.ints(0, 3, sx * sy) >= thr).reshape(sx, sy)
             m.tables.append((x, y, allowed))
     return m
+
+
+# ----------------------------------------------------------------------------- optimisation
+
+def objective_weights(seed: int, n: int, wmin: int = 1, wmax: int = 9):
+    """Objective minimise sum_i w_i x_i with w_i uniform on [wmin, wmax]: (coefs, vars)."""
+    s = Stream(seed_for(CFG_LNS_OBJ, seed))
+    return [int(w) for w in s.ints(wmin, wmax, n)], list(range(n))
+
+
+def relax_masks(n: int, copies: int, frac: float, round_id: int, seed: int) -> np.ndarray:
+    """Neighbourhoods of one search round: (copies, n) booleans, True = the variable is reset
+    to its root domain.  Each variable is reset with probability frac (a uniform draw on
+    [0, 2^32) below frac * 2^32); a copy that resets none resets one drawn variable."""
+    s = Stream(seed_for(CFG_LNS_RELAX, (seed & 0xffffffff) ^ (round_id << 20)))
+    u = (s.u64(copies * n) >> np.uint64(32)).reshape(copies, n)
+    masks = u < np.uint64(int(frac * 4294967296.0))
+    pick = s.ints(0, n - 1, copies)
+    for c in range(copies):
+        if not masks[c].any():
+            masks[c, pick[c]] = True
+    return masks
+
+
+def small_optimisation(seed: int, n: int = 9, d: int = 9, rows: int = 3):
+    """A small optimisation problem for exact checks: n vars on 0..d-1, one alldifferent over
+    all of them, `rows` linear rows (as in lin_alldiff, theta 0.6), weights on [1, 9]."""
+    m = lin_alldiff(seed, n=n, dmax=d - 1, rows=rows, kmin=2, kmax=min(5, n), groups=1, gsize=n,
+                    theta=0.6)
+    m.name = f"opt-s{seed & 0xffff:04x}"
+    return m, objective_weights(seed, n)
+
