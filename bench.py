@@ -537,12 +537,14 @@ class LNSRound(RBBatch):
         self.value = self.search.value
         self.bound = self.value - 1
         self.masks = I.relax_masks(self.model.n, self.COPIES, self.FRAC, 1000, 1)
-        self.probs = [lns.neighbourhood(self.search.base, self.inc, mk, self.obj, self.bound)
-                      for mk in self.masks]
+        self.bounded = self.search.base.clone()
+        self.bounded.post_lin(self.obj[0], self.obj[1], self.bound)
+        _, _, lo0 = self.bounded.layout()
+        roots = lns.neighbourhood_roots(self.bounded.root_domains(), lo0, self.inc, self.masks)
         self.tiling = K.tiling(warps_per_block=4, smem_levels=4)
         self.tune_entry = {"calib": None}
         self.lim = K.limits(node_limit=self.NODE_LIMIT)
-        self.b = K.Batch(self.probs)
+        self.b = K.Batch.from_roots(self.bounded, roots)
         self.b.stream = stream
         self.b.set_tiling(self.tiling)
         self.b.bind(K.CSP_FIRST, stream)

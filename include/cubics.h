@@ -209,6 +209,14 @@ const char *csp_strerror(int code);
  * atomic ticket and its warps share that instance's subtrees.  The handles must outlive the
  * batch; their models are encoded at csp_batch_create. */
 int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count);
+
+/* A batch of `count` copies of `base` that differ only in their root domains: copy i starts
+ * from host_roots[i*n*W .. (i+1)*n*W) intersected with the root domains of `base` (layout of
+ * csp_layout).  The model is encoded once and the copies share its constraints.  `base` must
+ * outlive the batch and stay unchanged.  The paper has no counterpart: the neighbourhoods of
+ * large neighbourhood search (Section 4) are such copies.  Host only. */
+int csp_batch_create_roots(csp_batch_t **out, csp_t *base, int32_t count,
+                           const uint32_t *host_roots);
 int csp_batch_set_tiling(csp_batch_t *b, const csp_tiling *t);
 int csp_batch_workspace_bytes(const csp_batch_t *b, int32_t mode, size_t *bytes);
 int csp_batch_bind(csp_batch_t *b, void *dev, size_t bytes, void *cuda_stream);

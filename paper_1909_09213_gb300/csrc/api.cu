@@ -280,9 +280,15 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
     {
         std::vector<int> deg(n, 0), kne(n, 0), klin(n, 0), kad(n, 0), ktab(n, 0);
         std::vector<double> tight(n, 0.0);
-        std::vector<std::vector<int32_t>> nb(n);
+        // neighbour sets as a bit matrix (a row of n bits per variable): long rows, such as
+        // an objective bound over every variable, cost one bit per pair
+        const size_t nw64 = ((size_t)n + 63) / 64;
+        std::vector<uint64_t> nbm((size_t)n * nw64, 0ull);
         auto link = [&](int a, int b) {
-            if (a != b) { nb[a].push_back(b); nb[b].push_back(a); }
+            if (a != b) {
+                nbm[(size_t)a * nw64 + b / 64] |= 1ull << (b % 64);
+                nbm[(size_t)b * nw64 + a / 64] |= 1ull << (a % 64);
+            }
         };
         for (size_t k = 0; k < h->ne_x.size(); ++k) {
             const int x = h->ne_x[k], y = h->ne_y[k];
@@ -322,14 +328,15 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
         B[H_OFF_NB_START] = (uint32_t)B.size();
         uint32_t s0 = 0;
         for (int v = 0; v < n; ++v) {
-            std::sort(nb[v].begin(), nb[v].end());
-            nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
             put(s0);
-            s0 += (uint32_t)nb[v].size();
+            for (size_t k = 0; k < nw64; ++k) s0 += (uint32_t)__builtin_popcountll(nbm[(size_t)v * nw64 + k]);
         }
         put(s0);
         B[H_OFF_NB] = (uint32_t)B.size();
-        for (int v = 0; v < n; ++v) for (int32_t u : nb[v]) put((uint32_t)u);
+        for (int v = 0; v < n; ++v)                    // ascending neighbour indices
+            for (size_t k = 0; k < nw64; ++k)
+                for (uint64_t w = nbm[(size_t)v * nw64 + k]; w; w &= w - 1)
+                    put((uint32_t)(k * 64 + (size_t)__builtin_ctzll(w)));
     }
     align4();
     B[H_CONS_WORDS] = (uint32_t)B.size();
@@ -984,6 +991,33 @@ int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count) {
         sw += h->n;
     }
     b->sol_words = sw;
+    *out = b;
+    return CSP_OK;
+}
+
+int csp_batch_create_roots(csp_batch_t **out, csp_t *base, int32_t count, const uint32_t *roots) {
+    if (!out || !base || count < 1 || !roots) return CSP_EINVAL;
+    csp_batch *b = new csp_batch();
+    b->hs.assign((size_t)count, base);
+    const int W = base->W, n = base->n;
+    b->W = W;
+    b->nmax = n;
+    b->depth = n + 1;
+    b->R = record_words(n * W, W);
+    std::vector<uint32_t> B;
+    encode(base, W, B);
+    const size_t root = B[H_OFF_ROOT], S = (size_t)n * W;
+    b->arena.resize(B.size() * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const size_t off = B.size() * (size_t)i;
+        std::memcpy(&b->arena[off], B.data(), B.size() * 4);
+        for (size_t k = 0; k < S; ++k) b->arena[off + root + k] = B[root + k] & roots[S * i + k];
+        b->inst_off.push_back((int64_t)off);
+        b->sol_off.push_back((int64_t)n * i);
+    }
+    b->cons_max = (int)B[H_CONS_WORDS];
+    b->ntab_max = (int)B[H_N_TAB];
+    b->sol_words = (int64_t)n * count;
     *out = b;
     return CSP_OK;
 }

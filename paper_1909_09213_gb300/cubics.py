@@ -78,6 +78,7 @@ SIGNATURES = {
     "csp_destroy": (None, [_VP]),
     "csp_strerror": (C.c_char_p, [C.c_int]),
     "csp_batch_create": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.c_int32]),
+    "csp_batch_create_roots": (C.c_int, [C.POINTER(_VP), _VP, C.c_int32, _U32P]),
     "csp_batch_set_tiling": (C.c_int, [_VP, C.POINTER(csp_tiling)]),
     "csp_batch_workspace_bytes": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_size_t)]),
     "csp_batch_bind": (C.c_int, [_VP, _VP, C.c_size_t, _VP]),
@@ -370,6 +371,20 @@ class Batch:
         self.b = b
         self.ws = None
         self.stream = None
+
+    @classmethod
+    def from_roots(cls, base: "Csp", roots) -> "Batch":
+        """csp_batch_create_roots: copies of `base` with root domains roots[i] & base's
+        (roots: (count, n, W) uint32)."""
+        n, W, _ = base.layout()
+        r = np.ascontiguousarray(np.asarray(roots, dtype=np.uint32).reshape(-1, n * W))
+        bt = object.__new__(cls)
+        bt.problems = [base] * r.shape[0]
+        b = _VP()
+        _check(lib().csp_batch_create_roots(C.byref(b), base.h, r.shape[0], _ptr(r, _U32P)),
+               "csp_batch_create_roots")
+        bt.b, bt.ws, bt.stream, bt._roots = b, None, None, r
+        return bt
 
     def __del__(self):
         b = getattr(self, "b", None)

@@ -5,8 +5,9 @@ each with a different random subset of domains reset, and to share the intermedi
 solutions so that no copy looks for a worse one.  Here one round is one batched launch:
 
 * copy j of the round keeps the variables of its neighbourhood (a random subset) at their
-  root domains and fixes every other variable to the incumbent's value (csp_clone and
-  csp_fix_values on the host, encoded once per copy);
+  root domains and fixes every other variable to the incumbent's value: the copies of a
+  round share one encoding of the model and differ only in their root domains
+  (csp_batch_create_roots; `neighbourhood` builds one copy as a problem of its own);
 * every copy carries the bound  sum_i c_i x_i <= f* - 1  (f* the incumbent's objective), an
   int_lin_le row, so it can only return a better solution;
 * all copies are searched in one persistent launch (first solution each, a node limit per
@@ -45,6 +46,17 @@ def neighbourhood(base: K.Csp, incumbent, mask, obj, bound: int) -> K.Csp:
         c.fix_values(fixed, np.asarray(incumbent, dtype=np.int64)[fixed])
     c.post_lin(obj[0], obj[1], bound)
     return c
+
+
+def neighbourhood_roots(root, lo0: int, incumbent, masks) -> np.ndarray:
+    """Root domains of the copies: (copies, n, W) words; variable x of copy j keeps its root
+    domain where masks[j, x], else the single value incumbent[x]."""
+    root = np.asarray(root, dtype=np.uint32)
+    n, W = root.shape
+    b = np.asarray(incumbent, dtype=np.int64) - lo0
+    single = np.zeros((n, W), dtype=np.uint32)
+    single[np.arange(n), b // 32] = (np.uint32(1) << (b % 32).astype(np.uint32))
+    return np.where(np.asarray(masks, dtype=bool)[:, :, None], root[None], single[None])
 
 
 def share_best(value, sol):
@@ -133,9 +145,12 @@ class LNS:
         else:
             masks = I.relax_masks(n, self.copies, self.frac, r, self.seed + 7919 * self.rank)
             lim = K.limits(node_limit=self.node_limit)
-        bound = self.value - 1
-        probs = [neighbourhood(self.base, self.incumbent, m, self.obj, bound) for m in masks]
-        b = K.Batch(probs)
+        # the model under the bound, encoded once; the copies differ in their root domains
+        bounded = self.base.clone()
+        bounded.post_lin(self.obj[0], self.obj[1], self.value - 1)
+        _, _, lo0 = bounded.layout()
+        b = K.Batch.from_roots(bounded, neighbourhood_roots(bounded.root_domains(), lo0,
+                                                            self.incumbent, masks))
         if self.tiling is not None:
             b.set_tiling(self.tiling)
         if self.stream is not None:

@@ -25,8 +25,9 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
+@pytest.mark.parametrize("build", ["copies", "shared_encoding"])
 @pytest.mark.parametrize("seed", range(3))
-def test_round_verdicts_match_the_oracle(seed):
+def test_round_verdicts_match_the_oracle(seed, build):
     m, obj = I.small_optimisation(seed, n=9, d=9)
     om = O.OracleModel(m)
     r0 = O.solve(om, mode=1, cap=1, variant=1)
@@ -36,8 +37,15 @@ def test_round_verdicts_match_the_oracle(seed):
     base = K.Csp(m)
     for frac in (0.3, 0.6):
         masks = I.relax_masks(m.n, 24, frac, seed, 17)
-        probs = [lns.neighbourhood(base, inc, mk, obj, f0 - 1) for mk in masks]
-        rc, res = K.Batch(probs).solve(K.CSP_FIRST)
+        if build == "copies":
+            batch = K.Batch([lns.neighbourhood(base, inc, mk, obj, f0 - 1) for mk in masks])
+        else:
+            bounded = base.clone()
+            bounded.post_lin(obj[0], obj[1], f0 - 1)
+            _, _, lo0 = bounded.layout()
+            batch = K.Batch.from_roots(bounded, lns.neighbourhood_roots(bounded.root_domains(), lo0,
+                                                                        inc, masks))
+        rc, res = batch.solve(K.CSP_FIRST)
         assert rc == 0
         for mk, r in zip(masks, res):
             want = L.verdict(L.neighbourhood_model(m, inc, mk, obj, f0 - 1))

@@ -101,6 +101,26 @@ def test_clone_and_fix_match_the_oracle_neighbourhood(seed):
 
 
 @pytest.mark.skipif(not _lib_available(), reason="library not built")
+def test_shared_encoding_roots_equal_the_copies():
+    from paper_1909_09213_gb300 import cubics as K
+    from paper_1909_09213_gb300 import lns
+    m, obj = I.small_optimisation(4, n=9, d=9)
+    m.removed += [(0, 3), (8, 8)]
+    best, sol = L.optimum(m, obj)
+    base = K.Csp(m)
+    _, _, lo0 = base.layout()
+    masks = I.relax_masks(m.n, 16, 0.35, 2, 9)
+    roots = lns.neighbourhood_roots(base.root_domains(), lo0, sol, masks)
+    for mk, rt in zip(masks, roots):
+        assert np.array_equal(lns.neighbourhood(base, sol, mk, obj, best).root_domains(), rt)
+    b = K.Batch.from_roots(base, roots)                         # host only: encodes once
+    assert len(b.problems) == 16
+    with pytest.raises(K.CspError) as e:
+        K.Batch.from_roots(base, roots[:0])
+    assert e.value.code == K.CSP_EINVAL
+
+
+@pytest.mark.skipif(not _lib_available(), reason="library not built")
 def test_fix_values_validation_and_empty_domain():
     from paper_1909_09213_gb300 import cubics as K
     m = I.CspModel(n=3, lo=[0, 0, 0], hi=[3, 3, 3])
