@@ -1,0 +1,139 @@
+"""FlatZinc-subset front end (host only): parsed problems against the oracle and against the
+models they were written from.  The FlatZinc texts are written here or by flatzinc.write."""
+import numpy as np
+import pytest
+
+from oracle import lns_ref as L
+from oracle import oracle as O
+from paper_1909_09213_gb300 import flatzinc as F
+from paper_1909_09213_gb300 import instances as I
+
+
+def queens_fzn(N):
+    """N-queens in the usual flat form: rows 1..N, one alldifferent, two diagonal int_lin_ne
+    per pair."""
+    out = [f"var 1..{N}: q{i};" for i in range(1, N + 1)]
+    qs = ", ".join(f"q{i}" for i in range(1, N + 1))
+    out.append(f"array [1..{N}] of var int: q :: output_array([1..{N}]) = [{qs}];")
+    out.append("constraint all_different_int(q);")
+    for i in range(1, N + 1):
+        for j in range(i + 1, N + 1):
+            out.append(f"constraint int_lin_ne([1, -1], [q{i}, q{j}], {i - j});")
+            out.append(f"constraint int_lin_ne([1, -1], [q[{i}], q[{j}]], {j - i});")
+    out.append("solve satisfy;")
+    return "\n".join(out) + "\n"
+
+
+WORKED = """
+% the worked example of Section 1.1: x1 in 1..5, x2 in 1..10, x1 > 3, x1 < x2
+var 1..5: x1 :: output_var;
+var 1..10: x2 :: output_var;
+constraint int_lt(3, x1);
+constraint int_lt(x1, x2);
+solve satisfy;
+"""
+
+
+def count(model):
+    r = O.solve(O.OracleModel(model), variant=1)
+    return r.solutions, r.hash_sum, r.hash_xor
+
+
+def test_worked_example_has_eleven_solutions():
+    p = F.parse(WORKED)
+    assert p.names == ["x1", "x2"] and p.solve == "satisfy"
+    assert count(p.model)[0] == 11
+
+
+@pytest.mark.parametrize("N,want", [(4, 2), (6, 4), (8, 92)])
+def test_queens_counts(N, want):
+    p = F.parse(queens_fzn(N))
+    assert p.model.n == N and len(p.model.alldiff) == 1 and len(p.model.ne) == N * (N - 1)
+    assert count(p.model)[0] == want
+
+
+@pytest.mark.parametrize("k", range(40))
+def test_write_then_parse_keeps_the_solution_set(k):
+    m = I.random_tiny(I.seed_for(I.CFG_TINY, 91000 + k))
+    p = F.parse(F.write(m))
+
+    def values(mm, i):
+        cut = {v for (x, v) in mm.removed if x == i}
+        return [v for v in range(mm.lo[i], mm.hi[i] + 1) if v not in cut]
+
+    assert p.model.n == m.n
+    for i in range(m.n):
+        if values(m, i):                    # an empty domain is written as an unsatisfiable row
+            assert values(p.model, i) == values(m, i)
+    assert count(p.model) == count(m)
+
+
+def test_set_domains_tables_and_params():
+    text = """
+    int: k = 2;
+    array [1..4] of int: pairs = [0, 1, 2, 0];
+    var {0, 2, 3}: a;
+    var 0..3: b;
+    constraint table_int([a, b], pairs);
+    constraint int_ne(b, k);
+    solve satisfy;
+    """
+    p = F.parse(text)
+    assert sorted(p.model.removed) == [(0, 1)]
+    r = O.solve(O.OracleModel(p.model), cap=10, variant=1)
+    # (a, b) in {(0, 1), (2, 0)}, b != 2
+    assert sorted(map(tuple, r.sols.tolist())) == [(0, 1), (2, 0)]
+
+
+def test_lin_eq_and_le_rows():
+    text = """
+    var 0..9: x; var 0..9: y; var 0..30: s;
+    constraint int_lin_eq([1, 2, -1], [x, y, s], 0);
+    constraint int_le(s, 5);
+    constraint int_eq(x, 1);
+    solve satisfy;
+    """
+    p = F.parse(text)
+    r = O.solve(O.OracleModel(p.model), cap=100, variant=1)
+    got = sorted(map(tuple, r.sols.tolist()))
+    assert got == [(1, y, 1 + 2 * y) for y in range(0, 3)]
+
+
+def test_minimize_reads_the_objective():
+    # an objective variable tied to a weighted sum over a permutation
+    w = [4, 1, 3]
+    text = """
+    var 0..2: a; var 0..2: b; var 0..2: c; var 0..40: f;
+    constraint all_different_int([a, b, c]);
+    constraint int_lin_eq([4, 1, 3, -1], [a, b, c, f], 0);
+    solve minimize f;
+    """
+    p = F.parse(text)
+    assert p.solve == "minimize" and p.objective == ([1], [3])
+    best, _ = L.optimum(p.model, p.objective)
+    assert best == sum(k * wk for k, wk in enumerate(sorted(w, reverse=True)))
+    q = F.parse(text.replace("minimize", "maximize"))
+    best_max, _ = L.optimum(q.model, q.objective)
+    assert -best_max == sum(k * wk for k, wk in enumerate(sorted(w)))
+
+
+@pytest.mark.parametrize("bad", [
+    "var 0..3: x; var 0..3: y; constraint int_times(x, y, x); solve satisfy;",
+    "var bool: b; solve satisfy;",
+    "var 0..3: x; var 0..3: y; var 0..3: z; constraint table_int([x, y, z], [0, 0, 0]); solve satisfy;",
+    "var 0..3: x; var 0..3: y; var 0..3: z; constraint int_lin_ne([1, 1, 1], [x, y, z], 3); solve satisfy;",
+    "var 0..300: x; solve satisfy;",
+    "var 0..3: x; constraint int_ne(x, y); solve satisfy;",
+    "var 0..3: x;",
+])
+def test_outside_the_subset_is_rejected(bad):
+    with pytest.raises(ValueError):
+        F.parse(bad)
+
+
+def test_solution_output_format():
+    p = F.parse(queens_fzn(4))
+    s = F.format_solution(p, np.array([2, 4, 1, 3]))
+    assert s.splitlines() == ["q = array1d(1..4, [2, 4, 1, 3]);", "----------"]
+    w = F.parse(WORKED)
+    assert F.format_solution(w, [4, 7]).splitlines() == ["x1 = 4;", "x2 = 7;", "----------"]
