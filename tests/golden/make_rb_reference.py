@@ -44,7 +44,8 @@ def main(count=4096, budget=2_000_000):
             part.flush()
     rows = [done[i] for i in range(count)]
     with open(OUT, "w") as f:
-        f.write("# Oracle verdicts on the batched model-RB workload (instances.rb_batch, config 3),\n"
+        f.write("# Oracle verdicts on the batched model-RB workload (instances.rb_batch: 4096 instances, "
+                "n~U[20,60], d~U[8,32]),\n"
                 f"# first solution, node budget {budget}; written by tests/golden/make_rb_reference.py.\n"
                 "# index n d status nodes   (status 1 SAT, 0 UNSAT, -5 undecided)\n")
         for r in rows:
