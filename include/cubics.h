@@ -114,7 +114,7 @@ int csp_create(csp_t **out, int32_t n_vars, const int32_t *lo, const int32_t *hi
 int csp_remove_value(csp_t *h, int32_t var, int32_t value);
 
 /* x != y + c; y < 0 posts the unary x != c.  Propagation: when one side is fixed, the value
- * it forbids is removed from the other (Section 1.1, "constraints propagation"). */
+ * it forbids is removed from the other (Section 1.1, constraint propagation). */
 int csp_post_int_ne(csp_t *h, int32_t x, int32_t y, int32_t c);
 
 /* sum_{t<k} coef[t] * x_{vars[t]} <= rhs, bounds-consistent.  Repeated variables are merged
@@ -193,7 +193,7 @@ int csp_upload(csp_t *h, int32_t mode, int64_t cap);
 int csp_launch(csp_t *h, const csp_limits *lim);
 int csp_collect(csp_t *h, int32_t *sol_out);
 
-/* One fixpoint per domain state (test hook; Section 1.1 "constraints propagation").
+/* One fixpoint per domain state (test hook; Section 1.1, constraint propagation).
  * dom_in, dom_out: host arrays of count * n * W words (layout of csp_layout); failed: host
  * array of count int32 (1 = some domain became empty; dom_out is then unspecified). */
 int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom_out,

@@ -20,6 +20,11 @@
  *            rounding, not C truncation); repeated variables are merged, zero terms dropped;
  *   alldiff  value elimination from fixed members, failure when two members share a fixed
  *            value or when the union of the domains has fewer values than members;
+ *   alldiff_bc  (the stronger propagation of Section 4, second direction) bounds
+ *            consistency on the interval relaxation: a bound v of member i stays when the
+ *            other members can take pairwise distinct values, all different from v, each
+ *            within its own [min, max]; unsupported bounds are removed until all are
+ *            supported (holes are kept);
  *   table    full arc consistency on a binary relation;
  *   search   d-way branching on the first-fail variable (smallest domain, ties to the lowest
  *            index), values in ascending order; every fixpoint call is one node, every
@@ -46,6 +51,8 @@ typedef struct {
     const int32_t *tab_x, *tab_y;
     const int64_t *tab_off;          /* byte offset of table t's matrix in tab_allowed */
     const uint8_t *tab_allowed;      /* row a - lo_x, column b - lo_y, row-major */
+    int32_t n_adb;                   /* bounds-consistent alldifferent groups */
+    const int32_t *adb_start, *adb_var;
 } oracle_model;
 
 typedef struct {
@@ -216,6 +223,80 @@ static int prop_alldiff(const layout *L, uint8_t *d, int g, uint8_t *changed) {
     return ch;
 }
 
+/* Augmenting path from member j (Kuhn's bipartite matching): owner[v - base] is the member
+ * holding value v, -1 when free, -2 when reserved for the member whose bound is tested. */
+static int bc_augment(int j, const int64_t *lo, const int64_t *hi, int64_t base, int32_t *owner,
+                      uint8_t *seen) {
+    for (int64_t v = lo[j]; v <= hi[j]; v++) {
+        int64_t x = v - base;
+        if (seen[x] || owner[x] == -2) continue;
+        seen[x] = 1;
+        if (owner[x] < 0 || bc_augment(owner[x], lo, hi, base, owner, seen)) {
+            owner[x] = j;
+            return 1;
+        }
+    }
+    return 0;
+}
+
+/* v is a supported value for member i: the other k - 1 members can be matched to distinct
+ * values other than v inside their intervals (Hall's marriage condition) */
+static int bc_supported(int k, const int64_t *lo, const int64_t *hi, int i, int64_t v,
+                        int64_t base, int64_t span, int32_t *owner, uint8_t *seen) {
+    for (int64_t x = 0; x < span; x++) owner[x] = -1;
+    owner[v - base] = -2;
+    for (int j = 0; j < k; j++) {
+        if (j == i) continue;
+        memset(seen, 0, (size_t)span);
+        if (!bc_augment(j, lo, hi, base, owner, seen)) return 0;
+    }
+    return 1;
+}
+
+static int prop_alldiff_bc(const layout *L, uint8_t *d, int g, uint8_t *changed) {
+    const oracle_model *m = L->m;
+    int b0 = m->adb_start[g], b1 = m->adb_start[g + 1], k = b1 - b0;
+    if (k == 0) return 0;
+    int64_t base = INT64_MAX, top = INT64_MIN;
+    for (int s = b0; s < b1; s++) {
+        int i = m->adb_var[s];
+        if (m->lo[i] < base) base = m->lo[i];
+        if (m->hi[i] > top) top = m->hi[i];
+    }
+    int64_t span = top - base + 1;
+    int64_t *lo = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int64_t *hi = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int32_t *owner = (int32_t *)malloc(sizeof(int32_t) * (size_t)span);
+    uint8_t *seen = (uint8_t *)malloc((size_t)span);
+    int ch = 0, res = 0;
+    for (int again = 1; again && res == 0;) {
+        again = 0;
+        for (int s = 0; s < k; s++) {
+            int i = m->adb_var[b0 + s];
+            if (dsize(L, d, i) == 0) { res = -1; break; }
+            lo[s] = dmin(L, d, i);
+            hi[s] = dmax(L, d, i);
+        }
+        for (int s = 0; s < k && res == 0; s++) {
+            int i = m->adb_var[b0 + s];
+            for (int side = 0; side < 2 && res == 0; side++) {
+                for (;;) {
+                    if (dsize(L, d, i) == 0) { res = -1; break; }
+                    lo[s] = dmin(L, d, i);
+                    hi[s] = dmax(L, d, i);
+                    int64_t v = side == 0 ? lo[s] : hi[s];
+                    if (bc_supported(k, lo, hi, s, v, base, span, owner, seen)) break;
+                    drop(L, d, i, v);
+                    ch = mark(changed, i);
+                    again = 1;
+                }
+            }
+        }
+    }
+    free(lo); free(hi); free(owner); free(seen);
+    return res < 0 ? -1 : ch;
+}
+
 static int allowed(const oracle_model *m, int t, int64_t a, int64_t b) {
     int x = m->tab_x[t], y = m->tab_y[t];
     int64_t sy = (int64_t)m->hi[y] - m->lo[y] + 1;
@@ -246,9 +327,12 @@ static int prop_table(const layout *L, uint8_t *d, int t, uint8_t *changed) {
 
 /* ------------------------------------------------------------------ fixpoints */
 
-static int n_props(const oracle_model *m) { return m->n_ne + m->n_lin + m->n_ad + m->n_tab; }
+static int n_props(const oracle_model *m) {
+    return m->n_ne + m->n_lin + m->n_ad + m->n_tab + m->n_adb;
+}
 
-/* propagator p in the global numbering ne..., lin..., alldiff..., table... */
+/* propagator p in the global numbering ne..., lin..., alldiff..., table..., alldiff_bc...
+ * (alldiff_bc evaluations are counted with the alldiff ones) */
 static int apply(const layout *L, uint8_t *d, int p, uint8_t *changed, int *kind) {
     const oracle_model *m = L->m;
     if (p < m->n_ne) { *kind = K_NE; return prop_ne(L, d, p, changed); }
@@ -257,8 +341,10 @@ static int apply(const layout *L, uint8_t *d, int p, uint8_t *changed, int *kind
     p -= m->n_lin;
     if (p < m->n_ad) { *kind = K_AD; return prop_alldiff(L, d, p, changed); }
     p -= m->n_ad;
-    *kind = K_TAB;
-    return prop_table(L, d, p, changed);
+    if (p < m->n_tab) { *kind = K_TAB; return prop_table(L, d, p, changed); }
+    p -= m->n_tab;
+    *kind = K_AD;
+    return prop_alldiff_bc(L, d, p, changed);
 }
 
 static int in_scope(const oracle_model *m, int p, int var) {
@@ -276,7 +362,11 @@ static int in_scope(const oracle_model *m, int p, int var) {
         return 0;
     }
     p -= m->n_ad;
-    return m->tab_x[p] == var || m->tab_y[p] == var;
+    if (p < m->n_tab) return m->tab_x[p] == var || m->tab_y[p] == var;
+    p -= m->n_tab;
+    for (int t = m->adb_start[p]; t < m->adb_start[p + 1]; t++)
+        if (m->adb_var[t] == var) return 1;
+    return 0;
 }
 
 static int any_empty(const layout *L, const uint8_t *d) {
@@ -350,7 +440,10 @@ static double eval_bytes(const layout *L, const uint8_t *d, int p, int W, int nc
         return 4.0 * W * 2.0 * k;
     }
     p -= m->n_ad;
-    return 4.0 * ((double)dsize(L, d, m->tab_x[p]) + 2.0) + 4.0 * ((double)dsize(L, d, m->tab_y[p]) + 2.0);
+    if (p < m->n_tab)
+        return 4.0 * ((double)dsize(L, d, m->tab_x[p]) + 2.0) + 4.0 * ((double)dsize(L, d, m->tab_y[p]) + 2.0);
+    p -= m->n_tab;
+    return 4.0 * W * 2.0 * (double)(m->adb_start[p + 1] - m->adb_start[p]);
 }
 
 /* variant 1: FIFO queue of propagators woken by the variables whose domain changed.
@@ -546,6 +639,10 @@ int oracle_check_solution(const oracle_model *m, const uint8_t *dom0, const int3
                 if (values[m->ad_var[s]] == values[m->ad_var[t]]) ok = 0;
     for (int t = 0; t < m->n_tab && ok; t++)
         if (!allowed(m, t, values[m->tab_x[t]], values[m->tab_y[t]])) ok = 0;
+    for (int g = 0; g < m->n_adb && ok; g++)
+        for (int s = m->adb_start[g]; s < m->adb_start[g + 1]; s++)
+            for (int t = s + 1; t < m->adb_start[g + 1]; t++)
+                if (values[m->adb_var[s]] == values[m->adb_var[t]]) ok = 0;
     layout_free(&L);
     return ok;
 }

@@ -24,7 +24,8 @@ class _Model(C.Structure):
                 ("lin_var", _I32P), ("lin_rhs", _I32P),
                 ("n_ad", C.c_int32), ("ad_start", _I32P), ("ad_var", _I32P),
                 ("n_tab", C.c_int32), ("tab_x", _I32P), ("tab_y", _I32P),
-                ("tab_off", _I64P), ("tab_allowed", _U8P)]
+                ("tab_off", _I64P), ("tab_allowed", _U8P),
+                ("n_adb", C.c_int32), ("adb_start", _I32P), ("adb_var", _I32P)]
 
 
 class _Stats(C.Structure):
@@ -104,13 +105,20 @@ class OracleModel:
         self.tab_y = i32([t[1] for t in m.tables])
         self.tab_off = np.asarray(offs, dtype=np.int64)
         self.tab_allowed = (np.concatenate(mats) if mats else np.zeros(1, np.uint8)).astype(np.uint8)
+        adb = getattr(m, "alldiff_bc", [])
+        adb_start, adb_var = [0], []
+        for g in adb:
+            adb_var += list(g)
+            adb_start.append(len(adb_var))
+        self.adb_start, self.adb_var = i32(adb_start), i32(adb_var)
         self.c = _Model(self.n, _p(self.lo, _I32P), _p(self.hi, _I32P),
                         len(ne), _p(self.ne_x, _I32P), _p(self.ne_y, _I32P), _p(self.ne_c, _I32P),
                         len(m.lin), _p(self.lin_start, _I32P), _p(self.lin_coef, _I32P),
                         _p(self.lin_var, _I32P), _p(self.lin_rhs, _I32P),
                         len(m.alldiff), _p(self.ad_start, _I32P), _p(self.ad_var, _I32P),
                         len(m.tables), _p(self.tab_x, _I32P), _p(self.tab_y, _I32P),
-                        _p(self.tab_off, _I64P), _p(self.tab_allowed, _U8P))
+                        _p(self.tab_off, _I64P), _p(self.tab_allowed, _U8P),
+                        len(adb), _p(self.adb_start, _I32P), _p(self.adb_var, _I32P))
 
     # ---------------------------------------------------------------- domains
     def root_flags(self) -> np.ndarray:

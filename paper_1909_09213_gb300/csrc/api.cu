@@ -1,7 +1,7 @@
 // Host side of the CUBICS C ABI: model building and validation, encoding into the device
 // layout of internal.h, workspace carving, and kernel launches (arxiv 1909.09213,
-// Section 2.1: the CPU builds the data structures and moves them to the GPU, control then
-// stays on the GPU until the results come back).
+// Section 2.1: the host encodes the problem once and copies it to device memory; the search
+// then runs on the device until its results are copied back).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -171,6 +171,8 @@ class Csp:
     """One CSP (X, D, C) built through csp_create / csp_post_* from a CspModel."""
 
     def __init__(self, model):
+        if getattr(model, "alldiff_bc", None):
+            raise ValueError("bounds-consistent alldifferent has no device propagator yet")
         L = lib()
         self.model = model
         h = _VP()

@@ -91,6 +91,7 @@ class CspModel:
     alldiff: list = field(default_factory=list)    # [vars]
     tables: list = field(default_factory=list)     # (x, y, allowed bool matrix)
     name: str = ""
+    alldiff_bc: list = field(default_factory=list) # [vars], bounds-consistent (oracle only)
 
     def n_constraints(self) -> int:
         return len(self.ne) + len(self.lin) + len(self.alldiff) + len(self.tables)
