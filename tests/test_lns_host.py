@@ -101,12 +101,14 @@ def test_clone_and_fix_match_the_oracle_neighbourhood(seed):
 
 
 @pytest.mark.skipif(not _lib_available(), reason="library not built")
-def test_shared_encoding_roots_equal_the_copies():
+@pytest.mark.parametrize("d", [9, 40, 100])          # one, two and four words per domain
+def test_shared_encoding_roots_equal_the_copies(d):
     from paper_1909_09213_gb300 import cubics as K
     from paper_1909_09213_gb300 import lns
-    m, obj = I.small_optimisation(4, n=9, d=9)
+    m, obj = I.small_optimisation(4, n=9, d=d)
     m.removed += [(0, 3), (8, 8)]
-    best, sol = L.optimum(m, obj)
+    sol = np.asarray(O.solve(O.OracleModel(m), mode=1, cap=1, variant=1).sols[0])
+    best = L.objective(obj, sol)
     base = K.Csp(m)
     _, _, lo0 = base.layout()
     masks = I.relax_masks(m.n, 16, 0.35, 2, 9)
