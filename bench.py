@@ -529,7 +529,7 @@ class LNSRound(RBBatch):
         self.lns_mod = lns
         # a mid-search incumbent: the first solution, improved by a few rounds (untimed)
         self.search = lns.LNS(self.model, self.obj, copies=self.COPIES, frac=self.FRAC,
-                              node_limit=self.NODE_LIMIT, seed=1)
+                              node_limit=self.NODE_LIMIT, seed=1, share=False)
         self.initial_value = self.search.initial()
         for r in range(self.WARM_ROUNDS):
             self.search.round(r)
@@ -586,8 +586,10 @@ class LNSRound(RBBatch):
         unsat = sum(r["status"] == 0 for r in self.res)
         # the whole search from scratch, 20 s at most (untimed by the events; wall clock)
         note("full LNS run")
+        # rank 0 alone runs this part: no exchange with the other ranks
         res = self.lns_mod.LNS(self.model, self.obj, copies=self.COPIES, frac=self.FRAC,
-                               node_limit=self.NODE_LIMIT, seed=2).run(rounds=200, time_budget_s=20)
+                               node_limit=self.NODE_LIMIT, seed=2, share=False).run(
+                                   rounds=200, time_budget_s=20)
         return {"copies": self.count, "sat": sat, "unsat": unsat,
                 "undecided_at_node_limit": self.count - sat - unsat,
                 "incumbent_of_the_timed_round": int(self.value),

@@ -110,14 +110,16 @@ class LNS:
     copies: neighbourhoods per round (one batched launch); frac: initial share of variables
     reset; grow: factor applied to frac after a round without improvement (capped at 1);
     node_limit: nodes per copy; seed: neighbourhood draws (instances.relax_masks, offset by
-    the rank so that ranks search different neighbourhoods)."""
+    the rank so that ranks search different neighbourhoods); share: exchange the incumbent
+    with the other torch.distributed ranks after every round (every rank must then run the
+    same number of rounds); False keeps the search on this rank."""
 
     def __init__(self, model, obj, copies: int = 256, frac: float = 0.2, grow: float = 1.5,
                  node_limit: int = 20_000, seed: int = 1, tiling: K.csp_tiling | None = None,
-                 stream=None, rank: int = 0):
+                 stream=None, rank: int = 0, share: bool = True):
         self.model, self.obj = model, obj
         self.copies, self.frac, self.grow = copies, frac, grow
-        self.node_limit, self.seed, self.rank = node_limit, seed, rank
+        self.node_limit, self.seed, self.rank, self.share = node_limit, seed, rank, share
         self.tiling, self.stream = tiling, stream
         self.base = K.Csp(model)
         self.incumbent = None
@@ -167,14 +169,16 @@ class LNS:
                     best_v, best_s = v, np.array(rj["solution"], dtype=np.int32)
             elif rj["status"] == 0 and full[j]:
                 proved = True           # no solution better than the incumbent exists at all
-        best_v, best_s = share_best(best_v, best_s)
+        if self.share:
+            best_v, best_s = share_best(best_v, best_s)
         improved = best_v is not None and best_v < self.value
         if improved:
             self.value, self.incumbent = best_v, best_s
             proved = False              # the proof was for the previous bound
         else:
             self.frac = min(1.0, self.frac * self.grow)
-        proved = _all_ranks(proved)
+        if self.share:
+            proved = _all_ranks(proved)
         sat = sum(x["status"] == 1 for x in res)
         unsat = sum(x["status"] == 0 for x in res)
         return RoundResult(r, float(masks.mean()), len(res), sat, unsat, len(res) - sat - unsat,
