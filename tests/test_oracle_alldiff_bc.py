@@ -114,3 +114,61 @@ def test_library_refuses_models_it_cannot_propagate():
     from paper_1909_09213_gb300 import cubics as K
     with pytest.raises(ValueError):
         K.Csp(_model([0, 0], [1, 1]))
+
+
+def _hall_interval_closure(doms):
+    """The reasoning planned for the device propagator, written plainly: while some interval
+    [a, b] (a a lower, b an upper bound of members) holds as many members' [min, max] as it
+    has values, no other member may take a bound inside it (its min moves above b, its max
+    below a); more members than values fails.  Holes are kept: a bound moves to the next
+    value of the domain."""
+    doms = [sorted(d) for d in doms]
+    while True:
+        if any(not d for d in doms):
+            return None
+        lo = [d[0] for d in doms]
+        hi = [d[-1] for d in doms]
+        changed = False
+        for a in sorted(set(lo)):
+            for b in sorted(set(hi)):
+                if b < a:
+                    continue
+                inside = [i for i in range(len(doms)) if a <= lo[i] and hi[i] <= b]
+                if len(inside) > b - a + 1:
+                    return None
+                if len(inside) < b - a + 1:
+                    continue
+                for j in range(len(doms)):
+                    if j in inside:
+                        continue
+                    keep = list(doms[j])
+                    if a <= lo[j] <= b:                  # the min moves above the interval
+                        keep = [v for v in keep if v > b]
+                    if a <= hi[j] <= b:                  # the max moves below it
+                        keep = [v for v in keep if v < a]
+                    if keep != doms[j]:
+                        doms[j] = keep
+                        changed = True
+                        if not keep:
+                            return None
+                lo = [d[0] if d else None for d in doms]
+                hi = [d[-1] if d else None for d in doms]
+                if any(d is None for d in lo):
+                    return None
+        if not changed:
+            return doms
+
+
+@pytest.mark.parametrize("seed", range(300))
+def test_hall_interval_reasoning_reaches_the_matching_closure(seed):
+    s = I.Stream(I.seed_for(I.CFG_TINY, 96000 + seed))
+    k = s.int(2, 6) if seed < 150 else s.int(5, 10)
+    w = 5 if seed < 150 else 9
+    lo = [int(s.int(0, w)) for _ in range(k)]
+    hi = [lo[i] + int(s.int(0, w)) for i in range(k)]
+    removed = [(i, int(s.int(lo[i], hi[i]))) for i in range(k) if hi[i] > lo[i] and s.int(0, 2) == 0]
+    m = _model(lo, hi, removed)
+    failed, d = _fix(m)
+    om = O.OracleModel(m)
+    want = _hall_interval_closure(om.flags_to_sets(om.root_flags()))
+    assert (failed, d) == (want is None, want)
