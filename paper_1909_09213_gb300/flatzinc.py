@@ -3,13 +3,19 @@ and builds the problem, the GPU solves it) into the CSP triple of Section 1.1.
 
 Supported subset (anything else is rejected with a ValueError naming the item):
 
-* variables: ``var lo..hi: x;`` and ``var {v1, v2, ...}: x;`` (integer domains of at most 256
-  consecutive values), ``var int: x = <int>;`` style fixed declarations are not needed by the
-  constraints below and are rejected; parameter arrays ``array [1..k] of int: a = [...];`` and
-  variable arrays ``array [1..k] of var int: xs = [x1, ...];`` (with ``output_array``);
+* variables: ``var lo..hi: x;``, ``var {v1, v2, ...}: x;`` (integer domains of at most 256
+  consecutive values), ``var bool: b;`` (0/1, printed false/true), ``var int: x = 3;`` and
+  ``var ...: x = y;`` (fixed values and aliases); parameter arrays ``array [1..k] of int: a =
+  [...];`` (also of bool) and variable arrays ``array [1..k] of var int: xs = [x1, ...];``
+  (with ``output_array``);
 * constraints: ``int_ne``, ``int_eq``, ``int_le``, ``int_lt``, ``int_lin_ne`` (the forms
   x != c and a x - a y != c), ``int_lin_le``, ``int_lin_eq`` (two rows), ``all_different_int``
-  (also ``fzn_all_different_int``), ``table_int`` over two variables;
+  (also ``fzn_all_different_int``), ``table_int`` over two variables; the boolean
+  ``bool_eq/ne/le/lt``, ``bool2int``, ``bool_not``, ``bool_clause``, ``array_bool_or``,
+  ``array_bool_and``, ``bool_lin_le/eq``; and the reified ``int_le/lt/eq/ne_reif``,
+  ``bool_le/lt/eq_reif``, ``int_lin_le/eq/ne_reif`` (linear rows with big-M terms from the
+  domain bounds, exact for these bounded domains; reified equalities add two hidden 0/1
+  variables);
 * ``solve satisfy;``, ``solve minimize x;``, ``solve maximize x;``.
 
 Every search step then runs in the library (``cubics.Csp``, ``lns.LNS``); this module only
@@ -32,6 +38,7 @@ class FznProblem:
     outputs: list = field(default_factory=list)   # ("var", name) | ("array", name, [dims], [idx])
     solve: str = "satisfy"                         # satisfy | minimize | maximize
     objective: tuple | None = None                 # (coefs, vars) to minimise
+    bools: set = field(default_factory=set)        # bool variables (printed true / false)
 
 
 _INT = r"-?\d+"
@@ -98,6 +105,8 @@ class _Builder:
         self.var_arrays = {}               # name -> list of var indices
         self.model = None
         self.outputs = []
+        self.bools = set()                 # indices of bool variables (printed true/false)
+        self.aliases = []                  # (var, token) from `var ...: x = token`
 
     # -- terms
     def var(self, tok: str) -> int:
@@ -114,13 +123,15 @@ class _Builder:
 
     def is_int(self, tok: str) -> bool:
         tok = tok.strip()
-        return re.fullmatch(_INT, tok) is not None or (tok in self.params and
-                                                        isinstance(self.params[tok], int))
+        return (re.fullmatch(_INT, tok) is not None or tok in ("true", "false") or
+                (tok in self.params and isinstance(self.params[tok], int)))
 
     def int(self, tok: str) -> int:
         tok = tok.strip()
         if re.fullmatch(_INT, tok):
             return int(tok)
+        if tok in ("true", "false"):
+            return 1 if tok == "true" else 0
         if tok in self.params and isinstance(self.params[tok], int):
             return self.params[tok]
         raise ValueError(f"expected an integer, got {tok}")
@@ -167,7 +178,7 @@ def parse(text: str) -> FznProblem:
             solve = _strip_annotations(st[len("solve"):]).strip()
             continue
         if head == "var":
-            m = re.fullmatch(r"var\s+(.+?)\s*:\s*([A-Za-z_]\w*)\s*(::.*)?", st)
+            m = re.fullmatch(r"var\s+(.+?)\s*:\s*([A-Za-z_]\w*)\s*(::[^=]*)?(=\s*(.+))?", st)
             if not m:
                 raise ValueError(f"cannot read declaration: {st}")
             dom, name, ann = m.group(1).strip(), m.group(2), m.group(3) or ""
@@ -176,11 +187,19 @@ def parse(text: str) -> FznProblem:
                 values = list(range(int(r.group(1)), int(r.group(2)) + 1))
             elif dom.startswith("{") and dom.endswith("}"):
                 values = [int(t) for t in _args(dom[1:-1])]
+            elif dom == "bool":
+                values = [0, 1]
+            elif dom == "int" and m.group(5) is not None and b.is_int(m.group(5)):
+                values = [b.int(m.group(5))]               # a constant declared as a variable
             else:
                 raise ValueError(f"unsupported domain for {name}: {dom}")
             if not values:
                 raise ValueError(f"empty domain for {name}")
-            b.declare(name, values)
+            i = b.declare(name, values)
+            if dom == "bool":
+                b.bools.add(i)
+            if m.group(5) is not None:
+                b.aliases.append((i, m.group(5).strip()))
             if "output_var" in ann:
                 b.outputs.append(("var", name))
             continue
@@ -211,9 +230,12 @@ def parse(text: str) -> FznProblem:
 
     model = CspModel(n=len(b.names), lo=list(b.lo), hi=list(b.hi), removed=list(b.removed),
                      name="fzn")
+    for i, tok in b.aliases:                       # var ...: x = 3  /  var ...: x = y
+        _post(b, model, f"int_eq({b.names[i]}, {tok})")
     for c in constraints:
         _post(b, model, c)
-    prob = FznProblem(model=model, names=list(b.names), index=dict(b.index), outputs=b.outputs)
+    prob = FznProblem(model=model, names=list(b.names), index=dict(b.index), outputs=b.outputs,
+                      bools=set(b.bools))
     if solve == "satisfy":
         prob.solve = "satisfy"
     else:
@@ -228,66 +250,190 @@ def parse(text: str) -> FznProblem:
     return prob
 
 
-def _post(b: _Builder, model: CspModel, c: str):
-    m = re.fullmatch(r"([A-Za-z_]\w*)\s*\((.*)\)", c)
-    if not m:
-        raise ValueError(f"cannot read constraint: {c}")
-    name, args = m.group(1), _args(m.group(2))
-    if name == "int_ne":
-        x, y = args
-        if b.is_int(x) and b.is_int(y):
-            if b.int(x) == b.int(y):
-                model.lin.append(([], [], -1))                 # never satisfied
-        elif b.is_int(y) or b.is_int(x):
-            v, k = (x, y) if b.is_int(y) else (y, x)
-            model.ne.append((b.var(v), -1, b.int(k)))
-        else:
-            model.ne.append((b.var(x), b.var(y), 0))
-    elif name in ("int_eq", "int_le", "int_lt"):
-        x, y = args
-        terms, rhs = [], 0
-        for tok, sign in ((x, 1), (y, -1)):
-            if b.is_int(tok):
-                rhs -= sign * b.int(tok)
+class _Poster:
+    """Posts FlatZinc constraints as the library's constraint kinds.  Reified comparisons
+    become linear rows with big-M terms taken from the domain bounds (exact for bounded
+    integer domains); an equality's reification goes through two auxiliary booleans."""
+
+    def __init__(self, b: _Builder, model: CspModel):
+        self.b, self.m = b, model
+
+    # -- helpers
+    def term(self, tok):
+        """(1, var) for a variable token, (None, value) for a constant."""
+        return (None, self.b.int(tok)) if self.b.is_int(tok) else (1, self.b.var(tok))
+
+    def row(self, coefs, vars_, rhs):
+        self.m.lin.append((list(coefs), list(vars_), int(rhs)))
+
+    def eq_row(self, coefs, vars_, rhs):
+        self.row(coefs, vars_, rhs)
+        self.row([-a for a in coefs], vars_, -rhs)
+
+    def aux_bool(self):
+        i = self.m.n
+        name = f"__aux{i}"
+        self.m.n += 1
+        self.m.lo.append(0)
+        self.m.hi.append(1)
+        self.b.index[name] = i
+        self.b.names.append(name)
+        return i
+
+    def bounds(self, coefs, vars_):
+        lo = sum(min(a * self.m.lo[v], a * self.m.hi[v]) for a, v in zip(coefs, vars_))
+        hi = sum(max(a * self.m.lo[v], a * self.m.hi[v]) for a, v in zip(coefs, vars_))
+        return lo, hi
+
+    def linear(self, pairs):
+        """pairs of (coef, token) -> (coefs, vars, constant part)"""
+        coefs, vars_, const = [], [], 0
+        for a, tok in pairs:
+            c, v = self.term(tok)
+            if c is None:
+                const += a * v
             else:
-                terms.append((sign, b.var(tok)))
-        coefs, vars_ = [t[0] for t in terms], [t[1] for t in terms]
-        if name == "int_lt":
-            rhs -= 1
-        model.lin.append((coefs, vars_, rhs))
-        if name == "int_eq":
-            model.lin.append(([-a for a in coefs], vars_, -rhs))
-    elif name in ("int_lin_le", "int_lin_eq", "int_lin_ne"):
-        coefs, vars_, rhs = b.list_of(args[0], "int"), b.list_of(args[1], "var"), b.int(args[2])
-        if len(coefs) != len(vars_):
-            raise ValueError(f"{name}: {len(coefs)} coefficients for {len(vars_)} variables")
-        if name == "int_lin_le":
-            model.lin.append((coefs, vars_, rhs))
-        elif name == "int_lin_eq":
-            model.lin.append((coefs, vars_, rhs))
-            model.lin.append(([-a for a in coefs], vars_, -rhs))
+                coefs.append(a)
+                vars_.append(v)
+        return coefs, vars_, const
+
+    def reif_le(self, coefs, vars_, c, r_tok):
+        """r <-> (sum coefs * vars <= c)"""
+        if self.b.is_int(r_tok):
+            if self.b.int(r_tok):
+                self.row(coefs, vars_, c)
+            else:
+                self.row([-a for a in coefs], vars_, -(c + 1))
+            return
+        r = self.b.var(r_tok)
+        smin, smax = self.bounds(coefs, vars_)
+        # r = 1 -> S <= c:       S + (smax - c) r <= smax
+        self.row(list(coefs) + [smax - c], list(vars_) + [r], smax)
+        # r = 0 -> S >= c + 1:  -S - (c + 1 - smin) r <= -(c + 1)
+        self.row([-a for a in coefs] + [-(c + 1 - smin)], list(vars_) + [r], -(c + 1))
+
+    def reif_eq(self, coefs, vars_, c, r_tok, negate=False):
+        """r <-> (S == c) (negate: r <-> (S != c)) through p <-> (S <= c), q <-> (S >= c);
+        p or q always holds, so S == c is p and q"""
+        p, q = self.aux_bool(), self.aux_bool()
+        self.reif_le(coefs, vars_, c, self.b.names[p])
+        self.reif_le([-a for a in coefs], vars_, -c, self.b.names[q])
+        if self.b.is_int(r_tok):
+            if bool(self.b.int(r_tok)) != negate:
+                self.row([-1, -1], [p, q], -2)           # p = q = 1
+            else:
+                self.row([1, 1], [p, q], 1)              # not both
+            return
+        r = self.b.var(r_tok)
+        if not negate:                                   # r = p and q
+            self.row([1, -1], [r, p], 0)
+            self.row([1, -1], [r, q], 0)
+            self.row([1, 1, -1], [p, q, r], 1)
+        else:                                            # r = not (p and q)
+            self.row([-1, -1], [r, p], -1)               # r >= 1 - p
+            self.row([-1, -1], [r, q], -1)               # r >= 1 - q
+            self.row([1, 1, 1], [r, p, q], 2)            # p = q = 1 -> r = 0
+
+    # -- constraints
+    def post(self, c: str):
+        b, model = self.b, self.m
+        m = re.fullmatch(r"([A-Za-z_]\w*)\s*\((.*)\)", c)
+        if not m:
+            raise ValueError(f"cannot read constraint: {c}")
+        name, args = m.group(1), _args(m.group(2))
+        if name in ("int_ne", "bool_ne"):
+            x, y = args
+            if b.is_int(x) and b.is_int(y):
+                if b.int(x) == b.int(y):
+                    model.lin.append(([], [], -1))       # never satisfied
+            elif b.is_int(y) or b.is_int(x):
+                v, k = (x, y) if b.is_int(y) else (y, x)
+                model.ne.append((b.var(v), -1, b.int(k)))
+            else:
+                model.ne.append((b.var(x), b.var(y), 0))
+        elif name in ("int_eq", "int_le", "int_lt", "bool_eq", "bool_le", "bool_lt", "bool2int"):
+            x, y = args
+            coefs, vars_, const = self.linear([(1, x), (-1, y)])
+            rhs = -const - (1 if name in ("int_lt", "bool_lt") else 0)
+            if name in ("int_eq", "bool_eq", "bool2int"):
+                self.eq_row(coefs, vars_, rhs)
+            else:
+                self.row(coefs, vars_, rhs)
+        elif name == "bool_not":
+            coefs, vars_, const = self.linear([(1, args[0]), (1, args[1])])
+            self.eq_row(coefs, vars_, 1 - const)
+        elif name in ("int_le_reif", "int_lt_reif", "bool_le_reif", "bool_lt_reif"):
+            x, y, r = args
+            coefs, vars_, const = self.linear([(1, x), (-1, y)])
+            self.reif_le(coefs, vars_, -const - (1 if name.endswith("lt_reif") else 0), r)
+        elif name in ("int_eq_reif", "int_ne_reif", "bool_eq_reif"):
+            x, y, r = args
+            coefs, vars_, const = self.linear([(1, x), (-1, y)])
+            self.reif_eq(coefs, vars_, -const, r, negate=name == "int_ne_reif")
+        elif name in ("int_lin_le", "int_lin_eq", "int_lin_ne", "bool_lin_le", "bool_lin_eq"):
+            coefs, vars_, rhs = b.list_of(args[0], "int"), b.list_of(args[1], "var"), b.int(args[2])
+            if len(coefs) != len(vars_):
+                raise ValueError(f"{name}: {len(coefs)} coefficients for {len(vars_)} variables")
+            if name.endswith("lin_le"):
+                self.row(coefs, vars_, rhs)
+            elif name.endswith("lin_eq"):
+                self.eq_row(coefs, vars_, rhs)
+            else:
+                _lin_ne(model, coefs, vars_, rhs)
+        elif name in ("int_lin_le_reif", "int_lin_eq_reif", "int_lin_ne_reif"):
+            coefs, vars_, rhs = b.list_of(args[0], "int"), b.list_of(args[1], "var"), b.int(args[2])
+            if len(coefs) != len(vars_):
+                raise ValueError(f"{name}: {len(coefs)} coefficients for {len(vars_)} variables")
+            if name == "int_lin_le_reif":
+                self.reif_le(coefs, vars_, rhs, args[3])
+            else:
+                self.reif_eq(coefs, vars_, rhs, args[3], negate=name == "int_lin_ne_reif")
+        elif name == "bool_clause":
+            pos, neg = b.list_of(args[0], "var"), b.list_of(args[1], "var")
+            # sum pos + sum (1 - neg) >= 1
+            self.row([-1] * len(pos) + [1] * len(neg), pos + neg, len(neg) - 1)
+        elif name in ("array_bool_or", "array_bool_and"):
+            xs, r = b.list_of(args[0], "var"), args[1]
+            k = len(xs)
+            if b.is_int(r):
+                if name == "array_bool_or":
+                    self.row([-1] * k, xs, -1) if b.int(r) else self.row([1] * k, xs, 0)
+                else:
+                    self.row([-1] * k, xs, -k) if b.int(r) else self.row([1] * k, xs, k - 1)
+                return
+            rv = b.var(r)
+            if name == "array_bool_or":                  # r = max(xs)
+                for x in xs:
+                    self.row([1, -1], [x, rv], 0)
+                self.row([1] + [-1] * k, [rv] + xs, 0)
+            else:                                        # r = min(xs)
+                for x in xs:
+                    self.row([1, -1], [rv, x], 0)
+                self.row([1] * k + [-1], xs + [rv], k - 1)
+        elif name in ("all_different_int", "fzn_all_different_int"):
+            vars_ = b.list_of(args[0], "var")
+            if len(set(vars_)) != len(vars_):
+                raise ValueError("all_different_int over a repeated variable")
+            model.alldiff.append(vars_)
+        elif name == "table_int":
+            vars_, flat = b.list_of(args[0], "var"), b.list_of(args[1], "int")
+            if len(vars_) != 2 or vars_[0] == vars_[1]:
+                raise ValueError("table_int is supported over two distinct variables only")
+            if len(flat) % 2:
+                raise ValueError("table_int: odd number of tuple entries")
+            x, y = vars_
+            import numpy as np
+            al = np.zeros((model.hi[x] - model.lo[x] + 1, model.hi[y] - model.lo[y] + 1), dtype=bool)
+            for a, c2 in zip(flat[0::2], flat[1::2]):
+                if model.lo[x] <= a <= model.hi[x] and model.lo[y] <= c2 <= model.hi[y]:
+                    al[a - model.lo[x], c2 - model.lo[y]] = True
+            model.tables.append((x, y, al))
         else:
-            _lin_ne(model, coefs, vars_, rhs)
-    elif name in ("all_different_int", "fzn_all_different_int"):
-        vars_ = b.list_of(args[0], "var")
-        if len(set(vars_)) != len(vars_):
-            raise ValueError("all_different_int over a repeated variable")
-        model.alldiff.append(vars_)
-    elif name == "table_int":
-        vars_, flat = b.list_of(args[0], "var"), b.list_of(args[1], "int")
-        if len(vars_) != 2 or vars_[0] == vars_[1]:
-            raise ValueError("table_int is supported over two distinct variables only")
-        if len(flat) % 2:
-            raise ValueError("table_int: odd number of tuple entries")
-        x, y = vars_
-        import numpy as np
-        al = np.zeros((model.hi[x] - model.lo[x] + 1, model.hi[y] - model.lo[y] + 1), dtype=bool)
-        for a, c2 in zip(flat[0::2], flat[1::2]):
-            if model.lo[x] <= a <= model.hi[x] and model.lo[y] <= c2 <= model.hi[y]:
-                al[a - model.lo[x], c2 - model.lo[y]] = True
-        model.tables.append((x, y, al))
-    else:
-        raise ValueError(f"constraint {name} is outside the supported subset")
+            raise ValueError(f"constraint {name} is outside the supported subset")
+
+
+def _post(b: _Builder, model: CspModel, c: str):
+    _Poster(b, model).post(c)
 
 
 def _lin_ne(model: CspModel, coefs, vars_, rhs):
@@ -363,15 +509,18 @@ def write(model: CspModel, names=None, solve: str = "satisfy", objective=None) -
 
 def format_solution(prob: FznProblem, values) -> str:
     """One solution in FlatZinc output form, followed by the separator line."""
+    def show(i):
+        v = int(values[i])
+        return ("true" if v else "false") if i in prob.bools else str(v)
+
     lines = []
     for o in prob.outputs:
         if o[0] == "var":
-            lines.append(f"{o[1]} = {int(values[prob.index[o[1]]])};")
+            lines.append(f"{o[1]} = {show(prob.index[o[1]])};")
         else:
             _, name, dims, idx = o
             d = ", ".join(f"{a}..{c}" for a, c in dims)
-            vals = ", ".join(str(int(values[i])) for i in idx)
-            lines.append(f"{name} = array{len(dims)}d({d}, [{vals}]);")
+            lines.append(f"{name} = array{len(dims)}d({d}, [{', '.join(show(i) for i in idx)}]);")
     lines.append("----------")
     return "\n".join(lines)
 

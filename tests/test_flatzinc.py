@@ -119,7 +119,8 @@ def test_minimize_reads_the_objective():
 
 @pytest.mark.parametrize("bad", [
     "var 0..3: x; var 0..3: y; constraint int_times(x, y, x); solve satisfy;",
-    "var bool: b; solve satisfy;",
+    "var float: f; solve satisfy;",
+    "var 0..3: x; var int: y = x; solve satisfy;",
     "var 0..3: x; var 0..3: y; var 0..3: z; constraint table_int([x, y, z], [0, 0, 0]); solve satisfy;",
     "var 0..3: x; var 0..3: y; var 0..3: z; constraint int_lin_ne([1, 1, 1], [x, y, z], 3); solve satisfy;",
     "var 0..300: x; solve satisfy;",
@@ -137,3 +138,88 @@ def test_solution_output_format():
     assert s.splitlines() == ["q = array1d(1..4, [2, 4, 1, 3]);", "----------"]
     w = F.parse(WORKED)
     assert F.format_solution(w, [4, 7]).splitlines() == ["x1 = 4;", "x2 = 7;", "----------"]
+
+
+# ---------------------------------------------------------------------------- booleans, reification
+
+def _solutions(text, n_orig):
+    """Solutions of the parsed model projected on its first n_orig (declared) variables."""
+    p = F.parse(text)
+    r = O.solve(O.OracleModel(p.model), cap=1 << 16, variant=1)
+    assert r.solutions < 1 << 16
+    proj = sorted({tuple(int(v) for v in s[:n_orig]) for s in r.sols})
+    assert len(proj) == r.solutions          # hidden variables are functions of the declared ones
+    return proj
+
+
+def _enumerate(doms, pred):
+    import itertools
+    return sorted(t for t in itertools.product(*doms) if pred(*t))
+
+
+R4, B = range(0, 4), range(0, 2)
+CASES = [
+    ("var 0..3: x; var 0..3: y; var bool: r; constraint int_le_reif(x, y, r);",
+     [R4, R4, B], lambda x, y, r: r == (x <= y)),
+    ("var 0..3: x; var 0..3: y; var bool: r; constraint int_lt_reif(x, y, r);",
+     [R4, R4, B], lambda x, y, r: r == (x < y)),
+    ("var 0..3: x; var 0..3: y; var bool: r; constraint int_eq_reif(x, y, r);",
+     [R4, R4, B], lambda x, y, r: r == (x == y)),
+    ("var 0..3: x; var 0..3: y; var bool: r; constraint int_ne_reif(x, y, r);",
+     [R4, R4, B], lambda x, y, r: r == (x != y)),
+    ("var 0..3: x; var bool: r; constraint int_eq_reif(x, 2, r);",
+     [R4, B], lambda x, r: r == (x == 2)),
+    ("var 0..3: x; var 0..3: y; var bool: r; constraint int_lin_le_reif([2, -1], [x, y], 1, r);",
+     [R4, R4, B], lambda x, y, r: r == (2 * x - y <= 1)),
+    ("var 0..3: x; var 0..3: y; var bool: r; constraint int_lin_eq_reif([1, 1], [x, y], 3, r);",
+     [R4, R4, B], lambda x, y, r: r == (x + y == 3)),
+    ("var 0..3: x; var 0..3: y; var bool: r; constraint int_lin_ne_reif([1, -2], [x, y], 0, r);",
+     [R4, R4, B], lambda x, y, r: r == (x - 2 * y != 0)),
+    ("var 0..3: x; var 0..3: y; constraint int_le_reif(x, y, true);",
+     [R4, R4], lambda x, y: x <= y),
+    ("var 0..3: x; var 0..3: y; constraint int_eq_reif(x, y, false);",
+     [R4, R4], lambda x, y: x != y),
+    ("var bool: a; var bool: b; var bool: c; constraint bool_clause([a, b], [c]);",
+     [B, B, B], lambda a, b, c: a or b or not c),
+    ("var bool: a; var bool: b; var bool: r; constraint array_bool_or([a, b], r);",
+     [B, B, B], lambda a, b, r: r == (a or b)),
+    ("var bool: a; var bool: b; var bool: r; constraint array_bool_and([a, b], r);",
+     [B, B, B], lambda a, b, r: r == (a and b)),
+    ("var bool: a; var bool: b; constraint array_bool_or([a, b], true);",
+     [B, B], lambda a, b: a or b),
+    ("var bool: a; var bool: b; constraint array_bool_and([a, b], false);",
+     [B, B], lambda a, b: not (a and b)),
+    ("var bool: a; var 0..1: i; constraint bool2int(a, i);",
+     [B, B], lambda a, i: a == i),
+    ("var bool: a; var bool: b; constraint bool_not(a, b);",
+     [B, B], lambda a, b: a != b),
+    ("var bool: a; var bool: b; var bool: r; constraint bool_eq_reif(a, b, r);",
+     [B, B, B], lambda a, b, r: r == (a == b)),
+    ("var bool: a; var bool: b; constraint bool_lt(a, b);",
+     [B, B], lambda a, b: a < b),
+    ("var bool: a; var bool: b; var bool: c; constraint bool_lin_le([1, 1, 1], [a, b, c], 1);",
+     [B, B, B], lambda a, b, c: a + b + c <= 1),
+    ("var 0..3: x; var 0..3: y = x; var int: z = 2; constraint int_ne(x, z);",
+     [R4, R4, range(2, 3)], lambda x, y, z: y == x and x != 2),
+]
+
+
+@pytest.mark.parametrize("k", range(len(CASES)))
+def test_boolean_and_reified_constraints(k):
+    text, doms, pred = CASES[k]
+    assert _solutions(text + " solve satisfy;", len(doms)) == _enumerate(doms, pred)
+
+
+def test_bool_output_and_arrays():
+    text = """
+    array [1..3] of bool: pat = [true, false, true];
+    var bool: a :: output_var;
+    var bool: b;
+    array [1..2] of var bool: ab :: output_array([1..2]) = [a, b];
+    constraint bool_clause([a], [b]);
+    solve satisfy;
+    """
+    p = F.parse(text)
+    assert p.bools == {0, 1}
+    out = F.format_solution(p, [1, 0])
+    assert out.splitlines() == ["a = true;", "ab = array1d(1..2, [true, false]);", "----------"]
