@@ -15,7 +15,9 @@ Supported subset (anything else is rejected with a ValueError naming the item):
   ``array_bool_and``, ``bool_lin_le/eq``; and the reified ``int_le/lt/eq/ne_reif``,
   ``bool_le/lt/eq_reif``, ``int_lin_le/eq/ne_reif`` (linear rows with big-M terms from the
   domain bounds, exact for these bounded domains; reified equalities add two hidden 0/1
-  variables);
+  variables); ``int_plus``, ``int_minus``, ``int_times`` with a constant factor,
+  ``int_max``, ``int_min`` (one hidden 0/1 variable), ``int_abs``, ``int_negate`` and
+  ``array_int_element`` (binary tables of the function), ``set_in``;
 * ``solve satisfy;``, ``solve minimize x;``, ``solve maximize x;``.
 
 Every search step then runs in the library (``cubics.Csp``, ``lns.LNS``); this module only
@@ -334,6 +336,36 @@ class _Poster:
             self.row([-1, -1], [r, q], -1)               # r >= 1 - q
             self.row([1, 1, 1], [r, p, q], 2)            # p = q = 1 -> r = 0
 
+    def function_table(self, x_tok, y_tok, f):
+        """y = f(x) as a binary table over the domains (f(x) None: x has no image)"""
+        b, model = self.b, self.m
+        if b.is_int(x_tok):
+            fx = f(b.int(x_tok))
+            if fx is None:
+                model.lin.append(([], [], -1))
+            elif b.is_int(y_tok):
+                if b.int(y_tok) != fx:
+                    model.lin.append(([], [], -1))
+            else:
+                self.eq_row([1], [b.var(y_tok)], fx)
+            return
+        x = b.var(x_tok)
+        if b.is_int(y_tok):
+            yv = b.int(y_tok)
+            model.removed += [(x, u) for u in range(model.lo[x], model.hi[x] + 1) if f(u) != yv]
+            return
+        y = b.var(y_tok)
+        if x == y:
+            model.removed += [(x, u) for u in range(model.lo[x], model.hi[x] + 1) if f(u) != u]
+            return
+        import numpy as np
+        al = np.zeros((model.hi[x] - model.lo[x] + 1, model.hi[y] - model.lo[y] + 1), dtype=bool)
+        for u in range(model.lo[x], model.hi[x] + 1):
+            fu = f(u)
+            if fu is not None and model.lo[y] <= fu <= model.hi[y]:
+                al[u - model.lo[x], fu - model.lo[y]] = True
+        model.tables.append((x, y, al))
+
     # -- constraints
     def post(self, c: str):
         b, model = self.b, self.m
@@ -410,6 +442,50 @@ class _Poster:
                 for x in xs:
                     self.row([1, -1], [rv, x], 0)
                 self.row([1] * k + [-1], xs + [rv], k - 1)
+        elif name in ("int_plus", "int_minus"):          # a + b = c  /  a - b = c
+            a, bb, cc = args
+            sign = 1 if name == "int_plus" else -1
+            coefs, vars_, const = self.linear([(1, a), (sign, bb), (-1, cc)])
+            self.eq_row(coefs, vars_, -const)
+        elif name == "int_times":                        # a * b = c, one factor constant
+            a, bb, cc = args
+            if b.is_int(a) or b.is_int(bb):
+                k, v = (b.int(a), bb) if b.is_int(a) else (b.int(bb), a)
+                coefs, vars_, const = self.linear([(k, v), (-1, cc)])
+                self.eq_row(coefs, vars_, -const)
+            else:
+                raise ValueError("int_times of two variables is outside the supported subset")
+        elif name in ("int_abs", "int_negate"):          # b = |a|  /  b = -a: a binary table
+            self.function_table(args[0], args[1], abs if name == "int_abs" else (lambda v: -v))
+        elif name == "array_int_element":                # c = as[idx] (1-based): a binary table
+            idx, arr, cc = args
+            vals = b.list_of(arr, "int")
+            self.function_table(idx, cc, lambda i: vals[i - 1] if 1 <= i <= len(vals) else None)
+        elif name in ("int_max", "int_min"):             # c = max(a, b)  /  c = min(a, b)
+            a, bb, cc = args
+            sgn = 1 if name == "int_max" else -1
+            # c >= a, c >= b (max) and c <= a or c <= b, chosen by a hidden 0/1 variable s
+            for t in (a, bb):
+                coefs, vars_, const = self.linear([(sgn, t), (-sgn, cc)])
+                self.row(coefs, vars_, -const)
+            s_ = self.aux_bool()
+            for t, on in ((a, 1), (bb, 0)):
+                coefs, vars_, const = self.linear([(sgn, cc), (-sgn, t)])
+                lo, hi = self.bounds(coefs, vars_)
+                big = max(hi + const, 0)
+                # s = on -> sgn (c - t) <= 0, else relaxed by `big`
+                self.row(coefs + [big if on else -big], vars_ + [s_], -const + (big if on else 0))
+        elif name == "set_in":                           # x in {..} or x in a..b
+            x, st = args
+            if st.startswith("{"):
+                keep = {b.int(t) for t in _args(st[1:-1])}
+            else:
+                r = re.fullmatch(rf"({_INT})\s*\.\.\s*({_INT})", st)
+                if not r:
+                    raise ValueError(f"set_in: unsupported set {st}")
+                keep = set(range(int(r.group(1)), int(r.group(2)) + 1))
+            v = b.var(x)
+            model.removed += [(v, u) for u in range(model.lo[v], model.hi[v] + 1) if u not in keep]
         elif name in ("all_different_int", "fzn_all_different_int"):
             vars_ = b.list_of(args[0], "var")
             if len(set(vars_)) != len(vars_):
