@@ -41,6 +41,8 @@ class FznProblem:
     solve: str = "satisfy"                         # satisfy | minimize | maximize
     objective: tuple | None = None                 # (coefs, vars) to minimise
     bools: set = field(default_factory=set)        # bool variables (printed true / false)
+    free: list = field(default_factory=list)       # variables a neighbourhood always resets:
+                                                   # introduced / defined, hidden, the objective
 
 
 _INT = r"-?\d+"
@@ -108,6 +110,7 @@ class _Builder:
         self.model = None
         self.outputs = []
         self.bools = set()                 # indices of bool variables (printed true/false)
+        self.introduced = set()            # variables annotated as introduced / defined
         self.aliases = []                  # (var, token) from `var ...: x = token`
 
     # -- terms
@@ -204,6 +207,8 @@ def parse(text: str) -> FznProblem:
                 b.aliases.append((i, m.group(5).strip()))
             if "output_var" in ann:
                 b.outputs.append(("var", name))
+            if "var_is_introduced" in ann or "is_defined_var" in ann:
+                b.introduced.add(i)
             continue
         if head == "array":
             m = re.fullmatch(r"array\s*\[(.+?)\]\s*of\s+(var\s+)?(int|[^:]+?)\s*:\s*([A-Za-z_]\w*)\s*"
@@ -247,6 +252,8 @@ def parse(text: str) -> FznProblem:
         v = b.var(m.group(2))
         prob.solve = m.group(1)
         prob.objective = ([1], [v]) if m.group(1) == "minimize" else ([-1], [v])
+        hidden = {i for i, nm in enumerate(prob.names) if nm.startswith("__aux")}
+        prob.free = sorted(b.introduced | hidden | {v})
     if not prob.outputs:
         prob.outputs = [("var", n) for n in b.names]
     return prob
@@ -623,7 +630,8 @@ def main(argv=None):
         print("==========" if st["solutions"] else "=====UNSATISFIABLE=====")
         return
     from . import lns
-    res = lns.LNS(prob.model, prob.objective).run(rounds=10**6, time_budget_s=a.time)
+    res = lns.LNS(prob.model, prob.objective, always_reset=prob.free).run(rounds=10**6,
+                                                                          time_budget_s=a.time)
     if res.best is None:
         print("=====UNSATISFIABLE=====")
         return

@@ -112,12 +112,15 @@ class LNS:
     node_limit: nodes per copy; seed: neighbourhood draws (instances.relax_masks, offset by
     the rank so that ranks search different neighbourhoods); share: exchange the incumbent
     with the other torch.distributed ranks after every round (every rank must then run the
-    same number of rounds); False keeps the search on this rank."""
+    same number of rounds); False keeps the search on this rank.  always_reset: variables
+    every neighbourhood resets (an objective variable, variables defined by others): fixing
+    them to the incumbent would leave no better solution in any neighbourhood."""
 
     def __init__(self, model, obj, copies: int = 256, frac: float = 0.2, grow: float = 1.5,
                  node_limit: int = 20_000, seed: int = 1, tiling: K.csp_tiling | None = None,
-                 stream=None, rank: int = 0, share: bool = True):
+                 stream=None, rank: int = 0, share: bool = True, always_reset=()):
         self.model, self.obj = model, obj
+        self.always_reset = np.asarray(list(always_reset), dtype=np.int64)
         self.copies, self.frac, self.grow = copies, frac, grow
         self.node_limit, self.seed, self.rank, self.share = node_limit, seed, rank, share
         self.tiling, self.stream = tiling, stream
@@ -146,6 +149,8 @@ class LNS:
             lim = K.limits(time_limit_ns=proof_time_ns)
         else:
             masks = I.relax_masks(n, self.copies, self.frac, r, self.seed + 7919 * self.rank)
+            if self.always_reset.size:
+                masks[:, self.always_reset] = True
             lim = K.limits(node_limit=self.node_limit)
         # the model under the bound, encoded once; the copies differ in their root domains
         bounded = self.base.clone()

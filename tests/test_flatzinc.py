@@ -245,3 +245,22 @@ def test_bool_output_and_arrays():
     assert p.bools == {0, 1}
     out = F.format_solution(p, [1, 0])
     assert out.splitlines() == ["a = true;", "ab = array1d(1..2, [true, false]);", "----------"]
+
+
+def test_minimize_marks_the_variables_a_neighbourhood_must_reset():
+    text = """
+    var 0..3: a; var 0..3: b;
+    var 0..20: cost :: output_var :: is_defined_var;
+    var bool: t :: var_is_introduced;
+    constraint int_lin_eq([2, 3, -1], [a, b, cost], 0) :: defines_var(cost);
+    constraint int_le_reif(a, b, t);
+    constraint int_eq_reif(a, 2, t);
+    solve minimize cost;
+    """
+    p = F.parse(text)
+    names = p.names
+    assert [names[i] for i in p.free] == ["cost", "t"] + [n for n in names if n.startswith("__aux")]
+    assert p.objective == ([1], [names.index("cost")])
+    best, _ = L.optimum(p.model, p.objective)
+    # t = (a <= b) = (a == 2): (a, b) in {(0..1, 0..a-1)} U {(2, 2..3)}; cheapest: a = 1, b = 0
+    assert best == 2
