@@ -89,3 +89,18 @@ def test_models_build_through_the_abi():
         p = K.Csp(m)
         n, W, lo0 = p.layout()
         assert n == m.n and W in (1, 2, 4, 8) and lo0 == min(m.lo)
+
+
+def test_encoded_root_domains_equal_the_oracle_domains():
+    # host-only: the encoder's root bitsets against the oracle's byte flags
+    from oracle import oracle as O
+    from _util import flags_to_bits
+    models = [I.queens(8), I.worked_example("domain", "table"), I.model_rb(3, 25, 20),
+              I.lin_alldiff(5, n=30, rows=6, groups=3)]
+    models += [I.random_tiny(I.seed_for(I.CFG_TINY, 95000 + k)) for k in range(60)]
+    for m in models:
+        p = K.Csp(m)
+        n, W, lo0 = p.layout()
+        om = O.OracleModel(m)
+        want = flags_to_bits(om, om.root_flags(), n, W, lo0).reshape(n, W)
+        assert np.array_equal(p.root_domains(), want), m.name
