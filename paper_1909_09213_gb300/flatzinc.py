@@ -49,16 +49,30 @@ _INT = r"-?\d+"
 
 
 def _split_statements(text: str):
-    """Statements separated by ';' outside brackets; comments (%) removed."""
-    lines = [ln.split("%", 1)[0] for ln in text.splitlines()]
+    """Statements separated by ';' outside brackets and string literals; comments (% to the
+    end of the line, outside string literals) removed."""
+    lines = []
+    for ln in text.splitlines():
+        quoted = False
+        for k, ch in enumerate(ln):
+            if ch == '"':
+                quoted = not quoted
+            elif ch == "%" and not quoted:
+                ln = ln[:k]
+                break
+        lines.append(ln)
     body = " ".join(lines)
-    out, depth, cur = [], 0, []
+    out, depth, cur, quoted = [], 0, [], False
     for ch in body:
-        if ch in "[({":
+        if ch == '"':
+            quoted = not quoted
+        elif quoted:
+            pass
+        elif ch in "[({":
             depth += 1
         elif ch in "])}":
             depth -= 1
-        if ch == ";" and depth == 0:
+        if ch == ";" and depth == 0 and not quoted:
             s = "".join(cur).strip()
             if s:
                 out.append(s)

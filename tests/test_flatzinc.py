@@ -264,3 +264,14 @@ def test_minimize_marks_the_variables_a_neighbourhood_must_reset():
     best, _ = L.optimum(p.model, p.objective)
     # t = (a <= b) = (a == 2): (a, b) in {(0..1, 0..a-1)} U {(2, 2..3)}; cheapest: a = 1, b = 0
     assert best == 2
+
+
+def test_strings_and_comments_in_output_items():
+    text = """
+    var 1..3: x :: output_var;   % a comment; with a semicolon
+    constraint int_ne(x, 2);
+    solve satisfy;
+    output ["x = ", show(x), ";\\n", "100%"];
+    """
+    p = F.parse(text)
+    assert p.names == ["x"] and count(p.model)[0] == 2
