@@ -555,11 +555,19 @@ class LNSRound(RBBatch):
         K._check(K.lib().csp_batch_launch(self.b.b, ctypes.byref(self.lim), 1), "csp_batch_launch")
 
     def e2e_step(self, K):
-        rc, res = self.b.solve(K.CSP_FIRST, lim=self.lim, use_graph=True, bind=False)
-        st = self.b.stats()
+        """A whole round through the public API: draw the neighbourhoods, build the copies
+        (one encoding, per-copy roots), upload, search, read the results back."""
+        from paper_1909_09213_gb300 import instances as I
+        self.e2e_round = getattr(self, "e2e_round", 2000) + 1
+        masks = I.relax_masks(self.model.n, self.COPIES, self.FRAC, self.e2e_round, 1)
+        _, _, lo0 = self.bounded.layout()
+        roots = self.lns_mod.neighbourhood_roots(self.bounded.root_domains(), lo0, self.inc, masks)
+        b = K.Batch.from_roots(self.bounded, roots)
+        b.set_tiling(self.tiling)
+        b.stream = self.b.stream
+        rc, res = b.solve(K.CSP_FIRST, lim=self.lim)
+        st = b.stats()
         st["nodes"] = sum(r["nodes"] for r in res)
-        st["h2d_bytes"] = 0
-        st["d2h_bytes"] = self.count * 40 + 4 * K.lib().csp_batch_solution_words(self.b.b)
         return st
 
     def parity(self, st):

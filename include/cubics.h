@@ -86,7 +86,8 @@ typedef struct {
     int64_t stored;          /* solutions written to sol_out */
     int32_t workers;         /* workers (warps) of the last launch */
     int32_t blocks;          /* blocks of the last launch */
-    int64_t h2d_bytes;       /* host-to-device bytes of the last upload */
+    int64_t h2d_bytes;       /* host-to-device bytes of the last upload (batches: uploaded
+                                since the previous collect) */
     int64_t d2h_bytes;       /* device-to-host bytes of the last collect */
     uint64_t wait_ns;        /* summed over workers: time spent waiting for work */
     uint64_t rounds;         /* fixpoint rounds (propagation passes over the changed scopes) */

@@ -848,6 +848,7 @@ struct csp_batch {
     int W = 1, R = 4, depth = 2, cons_max = 0;
     std::vector<uint32_t> arena;
     std::vector<int64_t> inst_off, sol_off;
+    int64_t pending_h2d = 0;         // bytes uploaded since the last collect
     int64_t sol_words = 0;
     csp_tiling tiling{0, 0, 0, 0};
     Shape shape;
@@ -1103,6 +1104,8 @@ static int batch_upload(csp_batch *b, int32_t mode) {
     if (b->mode != mode) drop_graph(b);
     b->mode = mode;
     b->uploaded = true;
+    b->pending_h2d += (int64_t)b->arena.size() * 4 + (int64_t)count * 16 +
+                      (b->brancher == CSP_BR_LEARNED ? (int64_t)CSP_MLP_PARAMS * 2 : 0);
     return CSP_OK;
 }
 
@@ -1172,6 +1175,10 @@ int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol) {
     fill_stats(&b->stats, g, 0);
     b->stats.ms = ms;
     b->stats.status = g.status;
+    b->stats.h2d_bytes = b->pending_h2d;
+    b->pending_h2d = 0;
+    b->stats.d2h_bytes = (int64_t)sizeof(g) + (int64_t)(count * sizeof(InstResult)) +
+                         (sol ? b->sol_words * 4 : 0);
     return g.status;
 }
 
