@@ -87,7 +87,7 @@ typedef struct {
     int32_t workers;         /* workers (warps) of the last launch */
     int32_t blocks;          /* blocks of the last launch */
     int64_t h2d_bytes;       /* host-to-device bytes of the last upload (batches: uploaded
-                                since the previous collect) */
+                                since the previous successful collect) */
     int64_t d2h_bytes;       /* device-to-host bytes of the last collect */
     uint64_t wait_ns;        /* summed over workers: time spent waiting for work */
     uint64_t rounds;         /* fixpoint rounds (propagation passes over the changed scopes) */
@@ -269,11 +269,11 @@ int csp_mlp_adam(float *master_dev, float *m_dev, float *v_dev, const float *gra
 
 /* ---------------------------------------------------------------- allocation-free search */
 
-/* csp_solve for callers that cannot allocate device memory: code that runs where
- * cudaMalloc is unavailable or forbidden (a caller inside a stream capture that must not
- * allocate, a plug-in whose host application owns every allocation, a real-time loop that
- * may not block in the allocator).  The paper has no counterpart; this is a library
- * convenience.
+/* csp_solve for callers that cannot allocate device memory.  Some callers may not call
+ * cudaMalloc at all: a plug-in loaded into a host application that owns every device
+ * allocation (through its own pool, under its own memory cap), or a latency-bound loop in
+ * which an allocation may block or synchronise the device.  The paper has no counterpart;
+ * this is a library convenience.
  *
  * Instead of a bound workspace, the search uses a scratch array inside the library's own
  * device image (CSP_NOALLOC_SCRATCH_BYTES = 16 MiB, reserved on every GPU that loads the
@@ -283,15 +283,17 @@ int csp_mlp_adam(float *master_dev, float *m_dev, float *v_dev, const float *gra
  * Inputs and outputs are the caller's: the handle h (model built with csp_create/post),
  * sol_out (host, cap * n int32; may be NULL when cap == 0) and the statistics read back
  * with csp_stats (stats.ms is 0: no events are created).  cuda_stream: cudaStream_t as
- * void* (NULL = legacy stream); the call is synchronous on it.
+ * void* (NULL = legacy stream); the call waits for the search on it before returning.
+ * The handle's own binding and upload (csp_bind, csp_upload) are neither used nor
+ * changed, whatever the call returns.
  *
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call
- * on a device shares the one array and leaves its contents behind; the counters that must
- * start at zero are cleared by each call.  Calls that overlap on the GPU (other host
- * threads, other streams) race on the array: serialise them.  Returns CSP_ENOMEM when the
- * problem, the launch shape (csp_set_tiling) and cap need more than the array holds, plus
- * the error codes of csp_solve. */
+ * The first call on each device does a one-time set-up: it looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Every call on a device shares the one array and leaves its contents
+ * behind; the counters that must start at zero are cleared by each call.  Calls that
+ * overlap on the GPU (other host threads, other streams) race on the array: serialise them.
+ * Returns CSP_ENOMEM when the problem, the launch shape (csp_set_tiling) and cap need more
+ * than the array holds, plus the error codes of csp_solve. */
 #define CSP_NOALLOC_SCRATCH_BYTES (16u << 20)
 int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
                       const csp_limits *lim, void *cuda_stream);

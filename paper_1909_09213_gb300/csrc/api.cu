@@ -136,6 +136,17 @@ struct Carver {
 
 // ---------------------------------------------------------------------------- handle
 
+// Layout of one single-problem workspace: the launch shape and the byte offset of every
+// region.  Planning fills one of these without touching the handle, which takes it over
+// only once the call that planned it can no longer fail for want of space.
+struct Plan {
+    Shape shape;
+    int R = 0, depth = 0;
+    size_t o_inst = 0, o_off = 0, o_g = 0, o_team = 0, o_qseq = 0, o_qrec = 0, o_spill = 0,
+           o_sols = 0, o_mlp_params = 0, o_mlp_packed = 0;
+    size_t bytes = 0;
+};
+
 struct csp {
     int32_t n = 0;
     std::vector<int32_t> lo, hi;
@@ -161,10 +172,7 @@ struct csp {
     uint32_t *pin_block = nullptr;   // pinned host staging of the encoded problem
     size_t pin_words = 0;
     GState *pin_g = nullptr;         // pinned host copy of the launch counters
-    Shape shape;
-    size_t o_inst = 0, o_off = 0, o_g = 0, o_team = 0, o_qseq = 0, o_qrec = 0, o_spill = 0,
-           o_sols = 0, o_mlp_params = 0, o_mlp_packed = 0;
-    int R = 0, depth = 0;
+    Plan plan;                       // workspace layout of the last upload
     std::vector<uint16_t> mlp_params;    // learned brancher weights (bf16)
     csp_stats_t stats{};
 };
@@ -361,41 +369,44 @@ int cuda_status(cudaError_t e) {
     return CSP_ECUDA;
 }
 
-// Layout of a single-problem workspace for mode/cap under the current tiling.
-int plan_single(csp *h, int32_t mode, int64_t cap, size_t *bytes, std::vector<uint32_t> *blk) {
+// Layout of a single-problem workspace for mode/cap under the current tiling; `blk`
+// receives the encoded problem.  The handle is not modified.
+int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<uint32_t> *blk) {
     std::vector<uint32_t> local;
     std::vector<uint32_t> &B = blk ? *blk : local;
     encode(h, h->W, B);
+    Plan p;
     Carver c;
-    h->o_inst = c.take(B.size() * 4);
-    h->o_off = c.take(sizeof(int64_t));
+    p.o_inst = c.take(B.size() * 4);
+    p.o_off = c.take(sizeof(int64_t));
     if (mode == CSP_PROPAGATE) {
         const size_t sw = (size_t)h->n * h->W * 4;
-        h->o_qseq = c.take(sw * (size_t)cap);     // dom_in
-        h->o_qrec = c.take(sw * (size_t)cap);     // dom_out
-        h->o_sols = c.take(4 * (size_t)cap);      // failed
-        *bytes = c.off;
+        p.o_qseq = c.take(sw * (size_t)cap);     // dom_in
+        p.o_qrec = c.take(sw * (size_t)cap);     // dom_out
+        p.o_sols = c.take(4 * (size_t)cap);      // failed
+        p.bytes = c.off;
+        *P = p;
         return CSP_OK;
     }
     const int R = record_words(h->n * h->W, h->W);
     const int depth = h->n + 1;
     const bool learned = h->brancher == CSP_BR_LEARNED;
-    Shape s;
     int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, learned, false,
-                        h->n, (int)B[H_N_TAB], &s);
+                        h->n, (int)B[H_N_TAB], &p.shape);
     if (rc) return rc;
-    h->shape = s;
-    h->R = R;
-    h->depth = depth;
-    h->o_g = c.take(sizeof(GState));
-    h->o_team = c.take(sizeof(Team));
-    h->o_qseq = c.take((size_t)s.qcap * 4);
-    h->o_qrec = c.take((size_t)s.qcap * R * 4);
-    h->o_spill = c.take((size_t)s.blocks * s.warps * depth * R * 4);
-    h->o_sols = c.take((size_t)std::max<int64_t>(cap, 1) * h->n * 4);
-    h->o_mlp_params = c.take(learned ? CSP_MLP_PARAMS * 2 : 0);
-    h->o_mlp_packed = c.take(learned ? CSP_MLP_PACKED_WORDS * 4 : 0);
-    *bytes = c.off;
+    const Shape &s = p.shape;
+    p.R = R;
+    p.depth = depth;
+    p.o_g = c.take(sizeof(GState));
+    p.o_team = c.take(sizeof(Team));
+    p.o_qseq = c.take((size_t)s.qcap * 4);
+    p.o_qrec = c.take((size_t)s.qcap * R * 4);
+    p.o_spill = c.take((size_t)s.blocks * s.warps * depth * R * 4);
+    p.o_sols = c.take((size_t)std::max<int64_t>(cap, 1) * h->n * 4);
+    p.o_mlp_params = c.take(learned ? CSP_MLP_PARAMS * 2 : 0);
+    p.o_mlp_packed = c.take(learned ? CSP_MLP_PACKED_WORDS * 4 : 0);
+    p.bytes = c.off;
+    *P = p;
     return CSP_OK;
 }
 
@@ -416,34 +427,34 @@ void set_learned_args(SearchArgs &A, const Shape &s, bool learned, const uint8_t
     A.warp_base = s.warp_base;
 }
 
-SearchArgs single_args(csp *h, int32_t mode, int64_t cap, const csp_limits *lim) {
+SearchArgs single_args(const csp *h, const Plan &P, uint8_t *w, int32_t mode, int64_t cap,
+                       const csp_limits *lim) {
     SearchArgs A{};
-    uint8_t *w = h->ws;
-    A.arena = (const uint32_t *)(w + h->o_inst);
-    A.inst_off = (const int64_t *)(w + h->o_off);
+    A.arena = (const uint32_t *)(w + P.o_inst);
+    A.inst_off = (const int64_t *)(w + P.o_off);
     A.sol_off = nullptr;
     A.n_inst = 1;
     A.mode = mode;
     A.batch = 0;
-    A.lsm = h->shape.lsm;
-    A.rmax = h->R;
-    A.depth = h->depth;
-    A.stage_words = h->shape.stage_words;
-    A.qmask = h->shape.qcap - 1;
+    A.lsm = P.shape.lsm;
+    A.rmax = P.R;
+    A.depth = P.depth;
+    A.stage_words = P.shape.stage_words;
+    A.qmask = P.shape.qcap - 1;
     A.flags = lim ? lim->flags : 0;
-    A.warps = h->shape.warps;
-    A.g = (GState *)(w + h->o_g);
-    A.teams = (Team *)(w + h->o_team);
-    A.qseq = (uint32_t *)(w + h->o_qseq);
-    A.qrec = (uint32_t *)(w + h->o_qrec);
-    A.spill = (uint32_t *)(w + h->o_spill);
-    A.sols = (int32_t *)(w + h->o_sols);
+    A.warps = P.shape.warps;
+    A.g = (GState *)(w + P.o_g);
+    A.teams = (Team *)(w + P.o_team);
+    A.qseq = (uint32_t *)(w + P.o_qseq);
+    A.qrec = (uint32_t *)(w + P.o_qrec);
+    A.spill = (uint32_t *)(w + P.o_spill);
+    A.sols = (int32_t *)(w + P.o_sols);
     A.cap = mode == CSP_FIRST ? 1 : cap;
     A.results = nullptr;
     A.node_limit = lim ? lim->node_limit : 0;
     A.deadline_ns = lim ? lim->time_limit_ns : 0;
     A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
-    set_learned_args(A, h->shape, h->brancher == CSP_BR_LEARNED, w, h->o_mlp_packed);
+    set_learned_args(A, P.shape, h->brancher == CSP_BR_LEARNED, w, P.o_mlp_packed);
     A.log_extra = 0;
     A.log_sample = 1;
     A.logbuf = nullptr;
@@ -661,13 +672,11 @@ int csp_set_brancher(csp_t *h, int32_t kind, const uint16_t *bf16_weights) {
 
 int csp_workspace_bytes(const csp_t *hc, int32_t mode, int64_t cap, size_t *bytes) {
     if (!hc || !bytes || mode < 0 || mode > 2 || cap < 0 || cap > INT32_MAX) return CSP_EINVAL;
-    csp tmp;
-    tmp.n = hc->n; tmp.lo = hc->lo; tmp.hi = hc->hi; tmp.present = hc->present;
-    tmp.ne_x = hc->ne_x; tmp.ne_y = hc->ne_y; tmp.ne_c = hc->ne_c;
-    tmp.lin = hc->lin; tmp.ad = hc->ad; tmp.tab = hc->tab;
-    tmp.lo0 = hc->lo0; tmp.W = hc->W; tmp.tiling = hc->tiling;
-    tmp.brancher = hc->brancher; tmp.part = hc->part; tmp.nparts = hc->nparts;
-    return plan_single(&tmp, mode, cap, bytes, nullptr);
+    Plan P;
+    const int rc = plan_single(hc, mode, cap, &P, nullptr);
+    if (rc) return rc;
+    *bytes = P.bytes;
+    return CSP_OK;
 }
 
 int csp_bind(csp_t *h, void *dev, size_t bytes, void *cuda_stream) {
@@ -688,12 +697,13 @@ int csp_bind(csp_t *h, void *dev, size_t bytes, void *cuda_stream) {
 int csp_upload(csp_t *h, int32_t mode, int64_t cap) {
     if (!h || mode < 0 || mode > 1 || cap < 0 || cap > INT32_MAX) return CSP_EINVAL;
     if (!h->ws) return CSP_ESTATE;
-    size_t need = 0;
-    int rc = plan_single(h, mode, cap, &need, &h->block);
+    Plan P;
+    std::vector<uint32_t> B;
+    int rc = plan_single(h, mode, cap, &P, &B);
     if (rc) return rc;
-    if (need > h->ws_bytes) return CSP_ENOMEM;
+    if (P.bytes > h->ws_bytes) return CSP_ENOMEM;
     // stage through pinned host memory: the encoded problem, then its block offset (0)
-    const size_t words = h->block.size() + 2;
+    const size_t words = B.size() + 2;
     if (h->pin_words < words) {
         if (h->pin_block) cudaFreeHost(h->pin_block);
         h->pin_block = nullptr;
@@ -709,16 +719,20 @@ int csp_upload(csp_t *h, int32_t mode, int64_t cap) {
         h->pin_g = nullptr;
         return CSP_ECUDA;
     }
+    // from here on the workspace is overwritten: the previous upload is no longer valid
+    h->uploaded = false;
+    h->plan = P;
+    h->block.swap(B);
     std::memcpy(h->pin_block, h->block.data(), h->block.size() * 4);
     h->pin_block[h->block.size()] = 0u;
     h->pin_block[h->block.size() + 1] = 0u;
-    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, h->pin_block, h->block.size() * 4,
+    cudaError_t e = cudaMemcpyAsync(h->ws + P.o_inst, h->pin_block, h->block.size() * 4,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->ws + h->o_off, h->pin_block + h->block.size(), sizeof(int64_t),
+        e = cudaMemcpyAsync(h->ws + P.o_off, h->pin_block + h->block.size(), sizeof(int64_t),
                             cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && h->brancher == CSP_BR_LEARNED)
-        e = upload_mlp(h->mlp_params, h->ws, h->o_mlp_params, h->o_mlp_packed, h->stream);
+        e = upload_mlp(h->mlp_params, h->ws, P.o_mlp_params, P.o_mlp_packed, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     h->stats.h2d_bytes = (int64_t)h->block.size() * 4 + (int64_t)sizeof(int64_t) +
@@ -731,23 +745,25 @@ int csp_upload(csp_t *h, int32_t mode, int64_t cap) {
 
 int csp_launch(csp_t *h, const csp_limits *lim) {
     if (!h || !h->uploaded) return CSP_ESTATE;
-    SearchArgs A = single_args(h, h->up_mode, h->up_cap, lim);
-    cudaError_t e = cudaMemsetAsync(h->ws + h->o_g, 0, sizeof(GState), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_team, 0, sizeof(Team), h->stream);
+    const Plan &P = h->plan;
+    SearchArgs A = single_args(h, P, h->ws, h->up_mode, h->up_cap, lim);
+    cudaError_t e = cudaMemsetAsync(h->ws + P.o_g, 0, sizeof(GState), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + P.o_team, 0, sizeof(Team), h->stream);
     if (e == cudaSuccess) e = launch_init_single(A, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess)
-        e = launch_search(h->W, h->shape.stage_words > 0, h->shape.ext, A, h->shape.blocks,
-                          h->shape.warps * 32, h->shape.smem, h->stream);
+        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.ext, A, P.shape.blocks,
+                          P.shape.warps * 32, P.shape.smem, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
-    h->stats.workers = h->shape.blocks * h->shape.warps;
-    h->stats.blocks = h->shape.blocks;
+    h->stats.workers = P.shape.blocks * P.shape.warps;
+    h->stats.blocks = P.shape.blocks;
     return cuda_status(e);
 }
 
 int csp_collect(csp_t *h, int32_t *sol_out) {
     if (!h || !h->uploaded || !h->pin_g) return CSP_ESTATE;
-    cudaError_t e = cudaMemcpyAsync(h->pin_g, h->ws + h->o_g, sizeof(GState),
+    const Plan &P = h->plan;
+    cudaError_t e = cudaMemcpyAsync(h->pin_g, h->ws + P.o_g, sizeof(GState),
                                     cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -757,7 +773,7 @@ int csp_collect(csp_t *h, int32_t *sol_out) {
     int64_t stored = std::min<int64_t>((int64_t)g.solutions, cap);
     if (h->up_mode == CSP_ALL) stored = std::min<int64_t>((int64_t)g.stored, cap);
     if (sol_out && stored > 0) {
-        e = cudaMemcpyAsync(sol_out, h->ws + h->o_sols, (size_t)stored * h->n * 4,
+        e = cudaMemcpyAsync(sol_out, h->ws + P.o_sols, (size_t)stored * h->n * 4,
                             cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_status(e);
@@ -788,22 +804,22 @@ int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom
     if (!h || count < 0 || (count > 0 && (!dom_in || !dom_out || !failed))) return CSP_EINVAL;
     if (!h->ws) return CSP_ESTATE;
     if (count == 0) return CSP_OK;
-    size_t need = 0;
+    Plan L;
     std::vector<uint32_t> B;
-    int rc = plan_single(h, CSP_PROPAGATE, count, &need, &B);
+    int rc = plan_single(h, CSP_PROPAGATE, count, &L, &B);
     if (rc) return rc;
-    if (need > h->ws_bytes) return CSP_ENOMEM;
-    h->uploaded = false;
+    if (L.bytes > h->ws_bytes) return CSP_ENOMEM;
+    h->uploaded = false;          // the workspace is overwritten
     const size_t sw = (size_t)h->n * h->W * 4;
-    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, B.data(), B.size() * 4,
+    cudaError_t e = cudaMemcpyAsync(h->ws + L.o_inst, B.data(), B.size() * 4,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->ws + h->o_qseq, dom_in, sw * count, cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(h->ws + L.o_qseq, dom_in, sw * count, cudaMemcpyHostToDevice, h->stream);
     PropArgs P{};
-    P.inst = (const uint32_t *)(h->ws + h->o_inst);
-    P.din = (const uint32_t *)(h->ws + h->o_qseq);
-    P.dout = (uint32_t *)(h->ws + h->o_qrec);
-    P.failed = (int32_t *)(h->ws + h->o_sols);
+    P.inst = (const uint32_t *)(h->ws + L.o_inst);
+    P.din = (const uint32_t *)(h->ws + L.o_qseq);
+    P.dout = (uint32_t *)(h->ws + L.o_qrec);
+    P.failed = (int32_t *)(h->ws + L.o_sols);
     P.count = count;
     const int cons4 = ((int)B[H_CONS_WORDS] + 3) & ~3;
     const int warps = 8;
@@ -816,9 +832,9 @@ int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom
     if (e == cudaSuccess)
         e = launch_propagate(h->W, P.stage_words > 0, P, blocks, warps * 32, smem, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dom_out, h->ws + h->o_qrec, sw * count, cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(dom_out, h->ws + L.o_qrec, sw * count, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(failed, h->ws + h->o_sols, 4 * (size_t)count, cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(failed, h->ws + L.o_sols, 4 * (size_t)count, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     return cuda_status(e);
 }
@@ -843,23 +859,30 @@ void csp_destroy(csp_t *h) {
 
 // ---------------------------------------------------------------------------- batches
 
+// Layout of a batch workspace (as Plan for one problem).
+struct BatchPlan {
+    Shape shape;
+    int R = 4;
+    size_t o_arena = 0, o_ioff = 0, o_soff = 0, o_g = 0, o_teams = 0, o_qseq = 0, o_qrec = 0,
+           o_spill = 0, o_sols = 0, o_res = 0, o_mlp_params = 0, o_mlp_packed = 0;
+    size_t bytes = 0;
+};
+
 struct csp_batch {
     std::vector<csp *> hs;
-    int W = 1, R = 4, depth = 2, cons_max = 0;
+    int W = 1, depth = 2, cons_max = 0;
     std::vector<uint32_t> arena;
     std::vector<int64_t> inst_off, sol_off;
     int64_t pending_h2d = 0;         // bytes uploaded since the last collect
     int64_t sol_words = 0;
     csp_tiling tiling{0, 0, 0, 0};
-    Shape shape;
+    BatchPlan plan;                  // workspace layout of the last upload
     uint8_t *ws = nullptr;
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool uploaded = false;
     int32_t mode = -1;
-    size_t o_arena = 0, o_ioff = 0, o_soff = 0, o_g = 0, o_teams = 0, o_qseq = 0, o_qrec = 0,
-           o_spill = 0, o_sols = 0, o_res = 0, o_mlp_params = 0, o_mlp_packed = 0;
     int nmax = 1, ntab_max = 0;
     int32_t brancher = CSP_BR_FIRST_FAIL;
     std::vector<uint16_t> mlp_params;
@@ -875,61 +898,63 @@ struct csp_batch {
 
 namespace {
 
-int plan_batch(csp_batch *b, int32_t mode, size_t *bytes) {
-    Shape s;
+// Layout of the batch's workspace under its current tiling, brancher and logging; the
+// batch is not modified.
+int plan_batch(const csp_batch *b, BatchPlan *P) {
+    BatchPlan p;
     const bool learned = b->brancher == CSP_BR_LEARNED;
-    b->R = record_words(b->nmax * b->W, b->W, b->logbuf ? LOG_EXTRA : 0);
-    int rc = make_shape(b->tiling, b->W, b->R, b->depth, b->cons_max, true, learned,
-                        b->logbuf != nullptr, b->nmax, b->ntab_max, &s);
+    p.R = record_words(b->nmax * b->W, b->W, b->logbuf ? LOG_EXTRA : 0);
+    int rc = make_shape(b->tiling, b->W, p.R, b->depth, b->cons_max, true, learned,
+                        b->logbuf != nullptr, b->nmax, b->ntab_max, &p.shape);
     if (rc) return rc;
-    (void)mode;
-    b->shape = s;
+    const Shape &s = p.shape;
     const size_t count = b->hs.size();
     Carver c;
-    b->o_arena = c.take(b->arena.size() * 4);
-    b->o_ioff = c.take(count * 8);
-    b->o_soff = c.take(count * 8);
-    b->o_g = c.take(sizeof(GState));
-    b->o_teams = c.take((size_t)s.blocks * sizeof(Team));
-    b->o_qseq = c.take((size_t)s.blocks * s.qcap * 4);
-    b->o_qrec = c.take((size_t)s.blocks * s.qcap * b->R * 4);
-    b->o_spill = c.take((size_t)s.blocks * s.warps * b->depth * b->R * 4);
-    b->o_sols = c.take((size_t)std::max<int64_t>(b->sol_words, 1) * 4);
-    b->o_res = c.take(count * sizeof(InstResult));
-    b->o_mlp_params = c.take(learned ? CSP_MLP_PARAMS * 2 : 0);
-    b->o_mlp_packed = c.take(learned ? CSP_MLP_PACKED_WORDS * 4 : 0);
-    *bytes = c.off;
+    p.o_arena = c.take(b->arena.size() * 4);
+    p.o_ioff = c.take(count * 8);
+    p.o_soff = c.take(count * 8);
+    p.o_g = c.take(sizeof(GState));
+    p.o_teams = c.take((size_t)s.blocks * sizeof(Team));
+    p.o_qseq = c.take((size_t)s.blocks * s.qcap * 4);
+    p.o_qrec = c.take((size_t)s.blocks * s.qcap * p.R * 4);
+    p.o_spill = c.take((size_t)s.blocks * s.warps * b->depth * p.R * 4);
+    p.o_sols = c.take((size_t)std::max<int64_t>(b->sol_words, 1) * 4);
+    p.o_res = c.take(count * sizeof(InstResult));
+    p.o_mlp_params = c.take(learned ? CSP_MLP_PARAMS * 2 : 0);
+    p.o_mlp_packed = c.take(learned ? CSP_MLP_PACKED_WORDS * 4 : 0);
+    p.bytes = c.off;
+    *P = p;
     return CSP_OK;
 }
 
 SearchArgs batch_args(csp_batch *b, const csp_limits *lim) {
     SearchArgs A{};
     uint8_t *w = b->ws;
-    A.arena = (const uint32_t *)(w + b->o_arena);
-    A.inst_off = (const int64_t *)(w + b->o_ioff);
-    A.sol_off = (const int64_t *)(w + b->o_soff);
+    A.arena = (const uint32_t *)(w + b->plan.o_arena);
+    A.inst_off = (const int64_t *)(w + b->plan.o_ioff);
+    A.sol_off = (const int64_t *)(w + b->plan.o_soff);
     A.n_inst = (int32_t)b->hs.size();
     A.mode = b->mode;
     A.batch = 1;
-    A.lsm = b->shape.lsm;
-    A.rmax = b->R;
+    A.lsm = b->plan.shape.lsm;
+    A.rmax = b->plan.R;
     A.depth = b->depth;
-    A.stage_words = b->shape.stage_words;
-    A.qmask = b->shape.qcap - 1;
+    A.stage_words = b->plan.shape.stage_words;
+    A.qmask = b->plan.shape.qcap - 1;
     A.flags = lim ? lim->flags : 0;
-    A.warps = b->shape.warps;
-    A.g = (GState *)(w + b->o_g);
-    A.teams = (Team *)(w + b->o_teams);
-    A.qseq = (uint32_t *)(w + b->o_qseq);
-    A.qrec = (uint32_t *)(w + b->o_qrec);
-    A.spill = (uint32_t *)(w + b->o_spill);
-    A.sols = (int32_t *)(w + b->o_sols);
+    A.warps = b->plan.shape.warps;
+    A.g = (GState *)(w + b->plan.o_g);
+    A.teams = (Team *)(w + b->plan.o_teams);
+    A.qseq = (uint32_t *)(w + b->plan.o_qseq);
+    A.qrec = (uint32_t *)(w + b->plan.o_qrec);
+    A.spill = (uint32_t *)(w + b->plan.o_spill);
+    A.sols = (int32_t *)(w + b->plan.o_sols);
     A.cap = 0;
-    A.results = (InstResult *)(w + b->o_res);
+    A.results = (InstResult *)(w + b->plan.o_res);
     A.node_limit = lim ? lim->node_limit : 0;
     A.deadline_ns = lim ? lim->time_limit_ns : 0;
     A.wait_limit_ns = (lim && lim->wait_limit_ns > 0) ? lim->wait_limit_ns : 60000000000LL;
-    set_learned_args(A, b->shape, b->brancher == CSP_BR_LEARNED, w, b->o_mlp_packed);
+    set_learned_args(A, b->plan.shape, b->brancher == CSP_BR_LEARNED, w, b->plan.o_mlp_packed);
     A.log_extra = b->logbuf ? LOG_EXTRA : 0;
     A.log_sample = b->log_sample;
     A.logbuf = b->logbuf;
@@ -942,15 +967,15 @@ SearchArgs batch_args(csp_batch *b, const csp_limits *lim) {
 }
 
 cudaError_t enqueue_batch(csp_batch *b, const SearchArgs &A) {
-    cudaError_t e = cudaMemsetAsync(b->ws + b->o_g, 0, sizeof(GState), b->stream);
+    cudaError_t e = cudaMemsetAsync(b->ws + b->plan.o_g, 0, sizeof(GState), b->stream);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(b->ws + b->o_teams, 0, (size_t)b->shape.blocks * sizeof(Team), b->stream);
+        e = cudaMemsetAsync(b->ws + b->plan.o_teams, 0, (size_t)b->plan.shape.blocks * sizeof(Team), b->stream);
     if (e == cudaSuccess)   // per-instance counters are accumulated atomically by every helper
-        e = cudaMemsetAsync(b->ws + b->o_res, 0, b->hs.size() * sizeof(InstResult), b->stream);
-    if (e == cudaSuccess) e = launch_init_batch(A, b->shape.blocks, b->stream);
+        e = cudaMemsetAsync(b->ws + b->plan.o_res, 0, b->hs.size() * sizeof(InstResult), b->stream);
+    if (e == cudaSuccess) e = launch_init_batch(A, b->plan.shape.blocks, b->stream);
     if (e == cudaSuccess)
-        e = launch_search(b->W, b->shape.stage_words > 0, b->shape.ext, A, b->shape.blocks,
-                          b->shape.warps * 32, b->shape.smem, b->stream);
+        e = launch_search(b->W, b->plan.shape.stage_words > 0, b->plan.shape.ext, A, b->plan.shape.blocks,
+                          b->plan.shape.warps * 32, b->plan.shape.smem, b->stream);
     return e;
 }
 
@@ -979,7 +1004,6 @@ int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count) {
     b->W = W;
     b->nmax = nmax;
     b->depth = nmax + 1;
-    b->R = record_words(nmax * W, W);
     int64_t sw = 0;
     for (csp *h : b->hs) {
         std::vector<uint32_t> B;
@@ -1004,7 +1028,6 @@ int csp_batch_create_roots(csp_batch_t **out, csp_t *base, int32_t count, const 
     b->W = W;
     b->nmax = n;
     b->depth = n + 1;
-    b->R = record_words(n * W, W);
     std::vector<uint32_t> B;
     encode(base, W, B);
     const size_t root = B[H_OFF_ROOT], S = (size_t)n * W;
@@ -1035,13 +1058,11 @@ int csp_batch_set_tiling(csp_batch_t *b, const csp_tiling *t) {
 
 int csp_batch_workspace_bytes(const csp_batch_t *bc, int32_t mode, size_t *bytes) {
     if (!bc || !bytes || mode < 0 || mode > 1) return CSP_EINVAL;
-    csp_batch tmp;
-    tmp.hs = bc->hs; tmp.W = bc->W; tmp.R = bc->R; tmp.depth = bc->depth;
-    tmp.cons_max = bc->cons_max; tmp.arena = bc->arena; tmp.sol_words = bc->sol_words;
-    tmp.tiling = bc->tiling; tmp.nmax = bc->nmax; tmp.brancher = bc->brancher;
-    tmp.logbuf = bc->logbuf;
-    tmp.ntab_max = bc->ntab_max;
-    return plan_batch(&tmp, mode, bytes);
+    BatchPlan P;
+    const int rc = plan_batch(bc, &P);
+    if (rc) return rc;
+    *bytes = P.bytes;
+    return CSP_OK;
 }
 
 int csp_batch_set_brancher(csp_batch_t *b, int32_t kind, const uint16_t *bf16_weights) {
@@ -1086,22 +1107,26 @@ int csp_batch_bind(csp_batch_t *b, void *dev, size_t bytes, void *cuda_stream) {
 
 static int batch_upload(csp_batch *b, int32_t mode) {
     if (!b->ws) return CSP_ESTATE;
-    size_t need = 0;
-    int rc = plan_batch(b, mode, &need);
+    BatchPlan P;
+    int rc = plan_batch(b, &P);
     if (rc) return rc;
-    if (need > b->ws_bytes) return CSP_ENOMEM;
+    if (P.bytes > b->ws_bytes) return CSP_ENOMEM;
+    // from here on the workspace is overwritten: the previous upload (and any graph that
+    // launches it) is no longer valid
+    b->uploaded = false;
+    drop_graph(b);
+    b->plan = P;
     const size_t count = b->hs.size();
-    cudaError_t e = cudaMemcpyAsync(b->ws + b->o_arena, b->arena.data(), b->arena.size() * 4,
+    cudaError_t e = cudaMemcpyAsync(b->ws + P.o_arena, b->arena.data(), b->arena.size() * 4,
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ws + b->o_ioff, b->inst_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
+        e = cudaMemcpyAsync(b->ws + P.o_ioff, b->inst_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ws + b->o_soff, b->sol_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
+        e = cudaMemcpyAsync(b->ws + P.o_soff, b->sol_off.data(), count * 8, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && b->brancher == CSP_BR_LEARNED)
-        e = upload_mlp(b->mlp_params, b->ws, b->o_mlp_params, b->o_mlp_packed, b->stream);
+        e = upload_mlp(b->mlp_params, b->ws, P.o_mlp_params, P.o_mlp_packed, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    if (b->mode != mode) drop_graph(b);
     b->mode = mode;
     b->uploaded = true;
     b->pending_h2d += (int64_t)b->arena.size() * 4 + (int64_t)count * 16 +
@@ -1119,8 +1144,8 @@ int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph) {
         if (!b->graph || b->graph_mode != b->mode || !same_limits(L, b->graph_lim)) {
             drop_graph(b);
             int bps = 0;   // sets the kernel's shared-memory attribute outside the capture
-            e = occupancy_search(b->W, b->shape.stage_words > 0, b->shape.ext, b->shape.warps * 32,
-                                 b->shape.smem, &bps);
+            e = occupancy_search(b->W, b->plan.shape.stage_words > 0, b->plan.shape.ext, b->plan.shape.warps * 32,
+                                 b->plan.shape.smem, &bps);
             cudaGraph_t g = nullptr;
             if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
@@ -1141,8 +1166,8 @@ int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph) {
         if (e == cudaSuccess) e = enqueue_batch(b, A);
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->ev1, b->stream);
-    b->stats.workers = b->shape.blocks * b->shape.warps;
-    b->stats.blocks = b->shape.blocks;
+    b->stats.workers = b->plan.shape.blocks * b->plan.shape.warps;
+    b->stats.blocks = b->plan.shape.blocks;
     return cuda_status(e);
 }
 
@@ -1151,12 +1176,12 @@ int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol) {
     const size_t count = b->hs.size();
     GState g;
     std::vector<InstResult> res(count);
-    cudaError_t e = cudaMemcpyAsync(&g, b->ws + b->o_g, sizeof(g), cudaMemcpyDeviceToHost, b->stream);
+    cudaError_t e = cudaMemcpyAsync(&g, b->ws + b->plan.o_g, sizeof(g), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(res.data(), b->ws + b->o_res, count * sizeof(InstResult),
+        e = cudaMemcpyAsync(res.data(), b->ws + b->plan.o_res, count * sizeof(InstResult),
                             cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess && sol)
-        e = cudaMemcpyAsync(sol, b->ws + b->o_sols, (size_t)b->sol_words * 4, cudaMemcpyDeviceToHost,
+        e = cudaMemcpyAsync(sol, b->ws + b->plan.o_sols, (size_t)b->sol_words * 4, cudaMemcpyDeviceToHost,
                             b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -1242,6 +1267,14 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return CSP_ECUDA; }
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return CSP_ECUDA;
+    // Lay the search out in the array as it would be in a bound workspace.  The plan is
+    // local: the handle's own binding, upload and plan are left as they were, so a workspace
+    // bound and uploaded earlier can still be launched after this call, whatever it returns.
+    Plan P;
+    std::vector<uint32_t> B;
+    int rc = plan_single(h, mode, cap, &P, &B);
+    if (rc) return rc;
+    if (P.bytes > (size_t)CSP_NOALLOC_SCRATCH_BYTES) return CSP_ENOMEM;
     if (!g_noalloc_ptr[dev]) {
         // set-up, once per device with that device current: the host-side name of the
         // array is not a device address, so look the address up
@@ -1252,57 +1285,46 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
         }
         g_noalloc_ptr[dev] = p;
     }
-    // lay the search out in the array as it would be in a bound workspace
-    uint8_t *const saved_ws = h->ws;
-    const size_t saved_bytes = h->ws_bytes;
-    const cudaStream_t saved_stream = h->stream;
-    size_t need = 0;
-    int rc = plan_single(h, mode, cap, &need, &h->block);
-    if (rc) return rc;
-    if (need > (size_t)CSP_NOALLOC_SCRATCH_BYTES) return CSP_ENOMEM;
-    h->ws = (uint8_t *)g_noalloc_ptr[dev];
-    h->ws_bytes = CSP_NOALLOC_SCRATCH_BYTES;
-    h->stream = (cudaStream_t)cuda_stream;
-    h->uploaded = false;
+    uint8_t *const ws = (uint8_t *)g_noalloc_ptr[dev];
+    const cudaStream_t st = (cudaStream_t)cuda_stream;
+    const bool learned = h->brancher == CSP_BR_LEARNED;
     const int64_t zero = 0;
-    SearchArgs A = single_args(h, mode, cap, lim);
-    cudaError_t e = cudaMemcpyAsync(h->ws + h->o_inst, h->block.data(), h->block.size() * 4,
-                                    cudaMemcpyHostToDevice, h->stream);
+    SearchArgs A = single_args(h, P, ws, mode, cap, lim);
+    cudaError_t e = cudaMemcpyAsync(ws + P.o_inst, B.data(), B.size() * 4,
+                                    cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->ws + h->o_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess && h->brancher == CSP_BR_LEARNED)
-        e = upload_mlp(h->mlp_params, h->ws, h->o_mlp_params, h->o_mlp_packed, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_g, 0, sizeof(GState), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->o_team, 0, sizeof(Team), h->stream);
-    if (e == cudaSuccess) e = launch_init_single(A, h->stream);
+        e = cudaMemcpyAsync(ws + P.o_off, &zero, sizeof(zero), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && learned)
+        e = upload_mlp(h->mlp_params, ws, P.o_mlp_params, P.o_mlp_packed, st);
+    // the launch counters and the work queue's state start at zero on every call
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + P.o_g, 0, sizeof(GState), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + P.o_team, 0, sizeof(Team), st);
+    if (e == cudaSuccess) e = launch_init_single(A, st);
     if (e == cudaSuccess)
-        e = launch_search(h->W, h->shape.stage_words > 0, h->shape.ext, A, h->shape.blocks,
-                          h->shape.warps * 32, h->shape.smem, h->stream);
+        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.ext, A, P.shape.blocks,
+                          P.shape.warps * 32, P.shape.smem, st);
     GState g;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&g, h->ws + h->o_g, sizeof(g), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        e = cudaMemcpyAsync(&g, ws + P.o_g, sizeof(g), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     int64_t stored = 0;
     if (e == cudaSuccess) {
         const int64_t c1 = mode == CSP_FIRST ? 1 : cap;
         stored = std::min<int64_t>(mode == CSP_ALL ? (int64_t)g.stored : (int64_t)g.solutions, c1);
         if (sol_out && stored > 0) {
-            e = cudaMemcpyAsync(sol_out, h->ws + h->o_sols, (size_t)stored * h->n * 4,
-                                cudaMemcpyDeviceToHost, h->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            e = cudaMemcpyAsync(sol_out, ws + P.o_sols, (size_t)stored * h->n * 4,
+                                cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         }
     }
-    h->ws = saved_ws;
-    h->ws_bytes = saved_bytes;
-    h->stream = saved_stream;
-    h->uploaded = false;
     if (e != cudaSuccess) return cuda_status(e);
     fill_stats(&h->stats, g, stored);
     h->stats.ms = 0.0;
     h->stats.status = g.status;
-    h->stats.workers = h->shape.blocks * h->shape.warps;
-    h->stats.blocks = h->shape.blocks;
-    h->stats.h2d_bytes = (int64_t)h->block.size() * 4 + (int64_t)sizeof(int64_t);
+    h->stats.workers = P.shape.blocks * P.shape.warps;
+    h->stats.blocks = P.shape.blocks;
+    h->stats.h2d_bytes = (int64_t)B.size() * 4 + (int64_t)sizeof(int64_t) +
+                         (learned ? (int64_t)CSP_MLP_PARAMS * 2 : 0);
     h->stats.d2h_bytes = (int64_t)sizeof(GState) + stored * h->n * 4;
     return g.status;
 }
