@@ -122,3 +122,29 @@ def test_subtree_logging_and_training():
     # better than the constant predictor (the target variance)
     assert tinfo["mse_per_epoch"][-1] < 0.9 * tinfo["target_variance"]
     assert len(params) == K.MLP_PARAMS
+
+
+@pytest.mark.parametrize("W", [2, 4, 8])
+def test_learned_order_at_wider_domains(W):
+    """The learned kernels for 2-, 4- and 8-word domains: the solution set, count and hash
+    equal first-fail's and the oracle's; only the tree may differ."""
+    from test_gpu_parity import mixed_model, pooled_wide_model, strided_queens
+    if W == 2:
+        models = [mixed_model(100 + k, 40, 5) for k in range(2)]
+    else:
+        stride, span = (13, 100) if W == 4 else (31, 250)
+        models = [strided_queens(9, stride), strided_queens(8, stride, alldiff=True, rows=True),
+                  pooled_wide_model(1002, span)]
+    w = _weights(11)
+    for m in models:
+        assert K.Csp(m).layout()[1] == W, m.name
+        r = O.solve(O.OracleModel(m), cap=100000, variant=1)
+        ff, ff_sols = _solve(m, K.CSP_BR_FIRST_FAIL)
+        le, le_sols = _solve(m, K.CSP_BR_LEARNED, w)
+        for k in ("solutions", "sol_hash_sum", "sol_hash_xor"):
+            assert le[k] == ff[k], (m.name, k)
+        assert (le["solutions"], le["sol_hash_sum"], le["sol_hash_xor"]) == (
+            r.solutions, r.hash_sum, r.hash_xor), m.name
+        if r.solutions <= 100000:              # otherwise each stores an arbitrary 100000
+            assert sorted(map(tuple, le_sols.tolist())) == sorted(map(tuple, ff_sols.tolist()))
+            assert sorted(map(tuple, le_sols.tolist())) == sorted(map(tuple, r.sols.tolist()))

@@ -60,6 +60,46 @@ def mixed_model(seed, span=40, n=7):
     return m
 
 
+def strided_queens(N, stride, alldiff=False, rows=False):
+    """N-queens over the values 0, stride, ..., (N-1) stride: the same search tree as
+    N-queens (the map k -> k stride is an isomorphism of the constraints), on a window of
+    (N-1) stride + 1 values, so W = 4 (stride 13) or W = 8 (stride 31).  With alldiff the
+    column constraints become one alldifferent group; rows adds two int_lin_le rows."""
+    hi = (N - 1) * stride
+    m = I.CspModel(n=N, lo=[0] * N, hi=[hi] * N, name=f"queens{N}x{stride}")
+    m.removed = [(i, v) for i in range(N) for v in range(hi + 1) if v % stride]
+    for i in range(N):
+        for j in range(i + 1, N):
+            if not alldiff:
+                m.ne.append((i, j, 0))
+            m.ne.append((i, j, stride * (i - j)))
+            m.ne.append((i, j, stride * (j - i)))
+    if alldiff:
+        m.alldiff.append(list(range(N)))
+    if rows:
+        m.lin.append(([1, 1], [0, 1], stride * (N - 1)))
+        m.lin.append(([1] * N, list(range(N)), stride * (N * (N - 1) // 2)))
+    return m
+
+
+def pooled_wide_model(seed, span, n=8, pool=9, keep=5):
+    """Every constraint kind over one window of `span` values; each domain keeps `keep`
+    values of a pool of `pool` values spread over the window (so that domains overlap)."""
+    s = I.Stream(seed)
+    lo0 = int(s.int(-20, 20))
+    m = I.CspModel(n=n, lo=[lo0] * n, hi=[lo0 + span - 1] * n, name=f"pooled-{span}-{seed}")
+    P = sorted(lo0 + int(v) for v in s.perm(span)[:pool])
+    for i in range(n):
+        kept = set(P[int(k)] for k in s.perm(pool)[:keep])
+        m.removed += [(i, v) for v in range(lo0, lo0 + span) if v not in kept]
+    m.ne += [(0, 1, 0), (2, 3, 0), (6, 7, 0), (1, 6, 0), (4, -1, P[0])]
+    m.lin.append(([1, -1, 2], [1, 2, 5], lo0 + int(s.int(span // 3, span // 2))))
+    m.lin.append(([-1, -1, 1], [0, 3, 6], -(lo0 + int(s.int(span // 4, span // 2)))))
+    m.alldiff.append([0, 2, 4, 5, 7])
+    m.tables.append((1, 5, (s.ints(0, 3, span * span) > 0).reshape(span, span)))
+    return m
+
+
 # ----------------------------------------------------------------------------- propagation
 
 def propagate_parity(m, rng, count):
@@ -178,6 +218,34 @@ def test_search_multiword_and_rb():
         search_parity(mixed_model(100 + seed, 40, 5), cap=100000)
     for k in range(6):
         search_parity(I.model_rb(I.seed_for(I.CFG_RB, 900 + k), 12, 6), cap=100000)
+
+
+@pytest.mark.parametrize("tname", ["auto", "spilling"])
+@pytest.mark.parametrize("N,stride,W", [(9, 13, 4), (10, 13, 4), (8, 31, 8), (9, 31, 8)])
+def test_search_strided_queens_wide_domains(N, stride, W, tname):
+    m = strided_queens(N, stride)
+    assert K.Csp(m).layout()[1] == W
+    st = search_parity(m, TILINGS[tname], cap=1000)
+    q = O.solve(O.OracleModel(I.queens(N)), variant=1)
+    assert (st["nodes"], st["fails"], st["solutions"]) == (q.nodes, q.fails, q.solutions)
+    assert st["solutions"] == queens_count(N)
+
+
+@pytest.mark.parametrize("stride,W", [(13, 4), (31, 8)])
+def test_search_alldiff_and_rows_wide_domains(stride, W):
+    for N in (8, 9):
+        m = strided_queens(N, stride, alldiff=True, rows=True)
+        assert K.Csp(m).layout()[1] == W
+        search_parity(m, cap=1000)
+
+
+@pytest.mark.parametrize("span,W", [(100, 4), (250, 8)])
+def test_search_every_kind_wide_domains(span, W):
+    for seed in range(6):
+        m = pooled_wide_model(1000 + seed, span)
+        assert K.Csp(m).layout()[1] == W
+        search_parity(m, cap=20000)
+        search_parity(m, TILINGS["spilling"], cap=0)
 
 
 def test_search_spill_heavy_deep_stack():
@@ -301,6 +369,22 @@ def test_small_workspace_is_enomem():
     assert L.csp_solve(p.h, K.CSP_ALL, 0, sols.ctypes.data_as(K._I32P), None) == K.CSP_ENOMEM
 
 
+def test_failed_upload_leaves_the_previous_upload_usable():
+    """On error the handle is unchanged: an upload that does not fit the bound workspace
+    (a larger cap) leaves the earlier upload in place, and it still launches correctly."""
+    m = I.queens(10)
+    orc = O.solve(O.OracleModel(m), cap=0, variant=1)
+    p = K.Csp(m)
+    p.bind(K.CSP_ALL, 0)
+    p.upload(K.CSP_ALL, 0)
+    assert K.lib().csp_upload(p.h, K.CSP_ALL, 10_000_000) == K.CSP_ENOMEM
+    p.launch()
+    assert p.collect() == 0
+    st = p.stats()
+    assert (st["solutions"], st["nodes"], st["fails"], st["sol_hash_sum"], st["sol_hash_xor"]) == (
+        orc.solutions, orc.nodes, orc.fails, orc.hash_sum, orc.hash_xor)
+
+
 def test_block_beyond_register_budget_is_einval():
     # the first-fail kernel is capped below 64 K / 1024 registers per thread: a 32-warp block
     # does not fit, a 16-warp block does
@@ -379,3 +463,29 @@ def test_batch_tilings_do_not_change_results():
         assert rc == 0
         out.append([(r["solutions"], r["nodes"], r["fails"]) for r in res])
     assert out[0] == out[1] == out[2]
+
+
+def test_batch_full_size_model_rb_verdicts_against_oracle_file():
+    """The benchmark's model-RB workload at full size (instances 0..511 of the 4096; n up to
+    60, d up to 32): every verdict equals the one the oracle wrote to
+    tests/golden/rb4096_oracle.txt (where it decided within its node budget), and every SAT
+    instance's solution satisfies the model.  The undecided ones get a node limit."""
+    golden = {}
+    for ln in open(os.path.join(GOLDEN, "rb4096_oracle.txt")):
+        if ln.strip() and not ln.startswith("#"):
+            i, n, d, status, nodes = map(int, ln.split())
+            golden[i] = (n, d, status)
+    models = I.rb_batch(512)
+    b = K.Batch([K.Csp(m) for m in models])
+    rc, res = b.solve(K.CSP_FIRST, lim=K.limits(node_limit=50_000_000), use_graph=True)
+    assert rc == 0
+    decided = 0
+    for i, (m, r) in enumerate(zip(models, res)):
+        n, d, status = golden[i]
+        assert (m.n, len(m.lo)) == (n, n)
+        if status >= 0:
+            decided += 1
+            assert r["status"] == status, (i, r["status"], status)
+        if r["status"] == 1:
+            assert O.check_solution(O.OracleModel(m), r["solution"]), i
+    assert decided >= 500

@@ -67,3 +67,34 @@ def test_adam_first_step_is_sign_times_lr():
     new, m, v = M.adam(flat, g, np.zeros(5), np.zeros(5), 1, lr=0.01)
     expect = 1 - 0.01 * np.sign(g) * (np.abs(g) / (np.abs(g) + 1e-8))
     assert np.allclose(new, expect)
+
+
+def test_activation_rounding_closed_form():
+    # one active path x3 -> h5 -> h7 -> s with unit weights downstream: the hidden values are
+    # rounded to bf16 (8 significant bits) when act_round is on
+    p = M.unflatten(np.zeros(M.N_PARAMS))
+    p["W2"][5, 7] = 1.0
+    p["w3"][7] = 1.0
+    x = np.zeros((1, 16))
+    x[0, 3] = 1.0
+    # 1 + 2^-8 + 2^-10 lies above the midpoint 1 + 2^-8 of 1 and 1 + 2^-7: rounds up
+    p["W1"][3, 5] = 1.0 + 2 ** -8 + 2 ** -10
+    s, _ = M.forward(M.flatten(p), x, act_round=True)
+    assert s[0] == 1.0 + 2 ** -7
+    s, _ = M.forward(M.flatten(p), x)
+    assert s[0] == 1.0 + 2 ** -8 + 2 ** -10
+    # exactly the midpoint: a tie, to the even neighbour 1
+    p["W1"][3, 5] = 1.0 + 2 ** -8
+    s, _ = M.forward(M.flatten(p), x, act_round=True)
+    assert s[0] == 1.0
+    # the second layer rounds too: H2 = bf16(3 * (1 + 2^-7)) = bf16(3 + 3 * 2^-7); the bf16
+    # spacing in [2, 4) is 2^-6, and 3 + 3 * 2^-7 = 3 + 1.5 * 2^-6 rounds to 3 + 2 * 2^-6
+    p["W1"][3, 5] = 1.0 + 2 ** -7
+    p["W2"][5, 7] = 3.0
+    s, (_, _, H1, Z2, H2) = M.forward(M.flatten(p), x, act_round=True)
+    assert H1[0, 5] == 1.0 + 2 ** -7 and Z2[0, 7] == 3.0 + 3 * 2 ** -7
+    assert s[0] == H2[0, 7] == 3.0 + 2 ** -5
+    # negative pre-activations are cut by the ReLU before rounding
+    p["W2"][5, 7] = -3.0
+    s, _ = M.forward(M.flatten(p), x, act_round=True)
+    assert s[0] == 0.0

@@ -362,6 +362,58 @@ def test_work_bytes_counts_ne_wakes():
     assert r.work_bytes == 12.0 * r.evals[0]
 
 
+# Hand-traced FIFO fixpoints of all-solution searches (first-fail, lowest index on ties,
+# values ascending).  At the root every propagator is queued once; at a child only those
+# over the branched variable; a propagator that changes a domain is queued again (it is in
+# the scope of the variable it changed).  Bytes per evaluation, with sizes taken before it:
+# int_ne 12; table 4 (|D(x)| + 2) + 4 (|D(y)| + 2); int_lin_le 4 W (2k + changed);
+# alldifferent 4 W 2k.
+
+def test_work_bytes_one_ne_by_hand():
+    # x, y in {0, 1}, x != y.  Root: 12 (nothing fixed).  x = 0: y loses 0 (12), queued
+    # again, nothing left to remove (12); x = 1 the same.  3 nodes, 2 solutions.
+    m = I.CspModel(n=2, lo=[0, 0], hi=[1, 1], ne=[(0, 1, 0)])
+    r = O.solve(O.OracleModel(m), variant=1, W=1)
+    assert (r.nodes, r.solutions) == (3, 2)
+    assert r.work_bytes == 12 + 2 * (12 + 12)
+
+
+def test_work_bytes_one_table_by_hand():
+    # x, y in {0, 1, 2} with every pair allowed: no evaluation changes anything.  Root:
+    # 4 (3 + 2) + 4 (3 + 2) = 40.  x = v: 4 (1 + 2) + 4 (3 + 2) = 32, then y = w:
+    # 4 (1 + 2) + 4 (1 + 2) = 24 for each of 3 values.  13 nodes.
+    m = I.CspModel(n=2, lo=[0, 0], hi=[2, 2], tables=[(0, 1, np.ones((3, 3), bool))])
+    r = O.solve(O.OracleModel(m), variant=1, W=1)
+    assert (r.nodes, r.solutions) == (13, 9)
+    assert r.work_bytes == 40 + 3 * (32 + 3 * 24)
+    # table sizes do not depend on W
+    assert O.solve(O.OracleModel(m), variant=1, W=4).work_bytes == r.work_bytes
+
+
+@pytest.mark.parametrize("W", [1, 2, 8])
+def test_work_bytes_one_row_by_hand(W):
+    # x, y in {0..3}, x + y <= 3 (k = 2): an evaluation is 4 W (4 + changed).
+    # Root: 4W*4 (no change).  x = 0: 16W, then y = 0..3: 4 x 16W.  x = 1: y <= 2 (20W),
+    # queued again (16W), then y = 0..2: 3 x 16W.  x = 2: 20W + 16W + 2 x 16W.  x = 3: y <= 0
+    # fixes y (20W + 16W): a solution without branching.  14 nodes, 10 solutions.
+    m = I.CspModel(n=2, lo=[0, 0], hi=[3, 3], lin=[([1, 1], [0, 1], 3)])
+    r = O.solve(O.OracleModel(m), variant=1, W=W)
+    assert (r.nodes, r.solutions) == (14, 10)
+    assert r.work_bytes == W * (16 + (16 + 64) + (36 + 48) + (36 + 32) + 36)
+
+
+@pytest.mark.parametrize("W", [1, 4])
+def test_work_bytes_one_alldiff_by_hand(W):
+    # x, y, z in {0, 1, 2}, all different (k = 3): an evaluation is 4 W 6.  Root: one
+    # evaluation.  x = v: v leaves y and z (one evaluation, queued again, a second one);
+    # then y (size 2, lowest index) = w: w leaves z (two evaluations again).  10 nodes.
+    m = I.CspModel(n=3, lo=[0, 0, 0], hi=[2, 2, 2], alldiff=[[0, 1, 2]])
+    r = O.solve(O.OracleModel(m), variant=1, W=W)
+    assert (r.nodes, r.solutions) == (10, 6)
+    e = 24 * W
+    assert r.work_bytes == e + 3 * (2 * e + 2 * (2 * e))
+
+
 # ----------------------------------------------------------------------------- generators
 
 def test_model_rb_shape():
