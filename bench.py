@@ -639,8 +639,8 @@ class LNSRound(RBBatch):
 def make_workload(name):
     if name == "queens16":
         return Queens(16)
-    if name == "queens14":
-        return Queens(14)
+    if name in ("queens14", "queens15"):
+        return Queens(int(name[6:]))
     if name == "rb4096":
         return RBBatch(4096)
     if name == "linad256":
@@ -788,7 +788,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="queens16",
-                    choices=["queens16", "queens14", "rb4096", "rb_learned", "linad256", "lns"])
+                    choices=["queens16", "queens15", "queens14", "rb4096", "rb_learned", "linad256",
+                             "lns"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

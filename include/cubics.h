@@ -64,9 +64,11 @@ typedef struct {
 typedef struct {
     int32_t blocks;           /* persistent blocks; 0 = resident blocks on every SM */
     int32_t warps_per_block;  /* workers per block (one warp each); 0 = 8.  A block must fit
-                                 the search kernel's register budget (the first-fail kernel
-                                 admits 25 warps for one-word domains, 21 for wider ones):
-                                 larger blocks make planning fail with CSP_EINVAL */
+                                 the search kernel's register budget (the first-fail kernels
+                                 admit 25 warps for one-word domains and 21 for wider ones;
+                                 the one for one-word int_ne problems of at most 32
+                                 variables admits 32): larger blocks make planning fail
+                                 with CSP_EINVAL */
     int32_t smem_levels;      /* search-stack levels kept in shared memory per worker */
     int32_t queue_records;    /* capacity of each work queue (power of two) */
 } csp_tiling;

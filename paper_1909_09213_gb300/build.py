@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcubics.so")
-SOURCES = ["api.cu", "kernels.cu", "mlp.cu"] + [f"kernels_w{w}{x}.cu" for w in (1, 2, 4, 8)
+SOURCES = ["api.cu", "kernels.cu", "mlp.cu", "kernels_w1r.cu"] + [f"kernels_w{w}{x}.cu" for w in (1, 2, 4, 8)
                                                   for x in ("", "x")]
 HEADERS = ["internal.h", "device.cuh", "search.cuh", "mlp.cuh", os.path.join("..", "..", "include", "cubics.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

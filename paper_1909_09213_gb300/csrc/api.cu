@@ -14,9 +14,9 @@
 #include "internal.h"
 
 namespace cubics {
-cudaError_t launch_search(int W, bool staged, bool ext, const SearchArgs &A, int blocks,
+cudaError_t launch_search(int W, bool staged, int kind, const SearchArgs &A, int blocks,
                           int threads, size_t smem, cudaStream_t st);
-cudaError_t occupancy_search(int W, bool staged, bool ext, int threads, size_t smem,
+cudaError_t occupancy_search(int W, bool staged, int kind, int threads, size_t smem,
                              int *blocks_per_sm);
 cudaError_t launch_init_single(const SearchArgs &A, cudaStream_t st);
 cudaError_t launch_init_batch(const SearchArgs &A, int teams, cudaStream_t st);
@@ -63,7 +63,7 @@ DeviceInfo device_info() {
 
 struct Shape {
     int blocks = 0, warps = 0, lsm = 0, qcap = 0, stage_words = 0;
-    bool ext = false;      // kernel with the learned brancher and subtree logging
+    int kind = KERN_PLAIN; // which search kernel (KERN_*)
     int mlp_words = 0;     // staged brancher weights (learned ordering)
     int feat_words = 0;    // per-warp feature tile (learned ordering)
     int list_words = 0;    // per-warp scheduled-table list (one-word tables)
@@ -73,10 +73,12 @@ struct Shape {
 
 // Resources of one search launch.  R and depth are record words and stack levels per
 // worker, cons the words of constraint data to stage in shared memory, nmax the largest
-// number of variables (feature tile rows when `learned`).
+// number of variables (feature tile rows when `learned`); `reg`: every problem of the launch
+// has FLAG_NE_REG (the register-held search kernel applies unless the learned brancher or
+// logging is on).
 int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batch, bool learned,
-               bool logging, int nmax, int ntab, Shape *s) {
-    s->ext = learned || logging;
+               bool logging, int nmax, int ntab, bool reg, Shape *s) {
+    s->kind = (learned || logging) ? KERN_EXT : reg ? KERN_REG : KERN_PLAIN;
     // one-word tables are revised from a per-warp list of the scheduled ones
     s->list_words = (W == 1 && ntab > 0) ? (ntab + 31) & ~31 : 0;
     s->warps = t.warps_per_block > 0 ? t.warps_per_block : 8;
@@ -109,7 +111,7 @@ int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batc
     // registers.  An explicit grid needs no device to be planned.
     int bps = 0;
     const cudaError_t oe =
-        occupancy_search(W, s->stage_words > 0, s->ext, s->warps * 32, s->smem, &bps);
+        occupancy_search(W, s->stage_words > 0, s->kind, s->warps * 32, s->smem, &bps);
     if (oe != cudaSuccess) cudaGetLastError();
     if (oe == cudaSuccess && bps < 1) return CSP_EINVAL;
     if (t.blocks > 0) {
@@ -346,6 +348,22 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
                 for (uint64_t w = nbm[(size_t)v * nw64 + k]; w; w &= w - 1)
                     put((uint32_t)(k * 64 + (size_t)__builtin_ctzll(w)));
     }
+    // int_ne offset masks for a search that keeps one-word domains in registers
+    const bool ne_only = h->lin.empty() && h->ad.empty() && h->tab.empty();
+    if (ne_only && W == 1 && n <= 32) {
+        flags |= FLAG_NE_REG;
+        while (B.size() & 1) B.push_back(0u);                 // 8-byte aligned pairs
+        const size_t nm = B.size();
+        B[H_OFF_NEMASK] = (uint32_t)nm;
+        B.resize(nm + (size_t)2 * 32 * n, 0u);
+        for (int v = 0; v < n; ++v)
+            for (uint32_t e : adj[v]) {                        // fixing v removes val + off from t
+                const int t = (int)(e & 0xffffu), off = (int)(int16_t)(e >> 16);
+                if (off < -31 || off > 31) continue;
+                const int bit = off + 31;
+                B[nm + 2 * ((size_t)v * 32 + t) + (bit >> 5)] |= 1u << (bit & 31);
+            }
+    }
     align4();
     B[H_CONS_WORDS] = (uint32_t)B.size();
     B[H_OFF_ROOT] = (uint32_t)B.size();
@@ -359,7 +377,7 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
     while (B.size() & 63) B.push_back(0u);
     B[H_TOTAL] = (uint32_t)B.size();
     B[H_R] = (uint32_t)record_words(S, W);
-    if (h->lin.empty() && h->ad.empty() && h->tab.empty()) flags |= FLAG_NE_ONLY;
+    if (ne_only) flags |= FLAG_NE_ONLY;
     B[H_FLAGS] = flags;
 }
 
@@ -392,7 +410,7 @@ int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<ui
     const int depth = h->n + 1;
     const bool learned = h->brancher == CSP_BR_LEARNED;
     int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], false, learned, false,
-                        h->n, (int)B[H_N_TAB], &p.shape);
+                        h->n, (int)B[H_N_TAB], (B[H_FLAGS] & FLAG_NE_REG) != 0, &p.shape);
     if (rc) return rc;
     const Shape &s = p.shape;
     p.R = R;
@@ -752,7 +770,7 @@ int csp_launch(csp_t *h, const csp_limits *lim) {
     if (e == cudaSuccess) e = launch_init_single(A, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess)
-        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.ext, A, P.shape.blocks,
+        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.kind, A, P.shape.blocks,
                           P.shape.warps * 32, P.shape.smem, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
     h->stats.workers = P.shape.blocks * P.shape.warps;
@@ -884,6 +902,7 @@ struct csp_batch {
     bool uploaded = false;
     int32_t mode = -1;
     int nmax = 1, ntab_max = 0;
+    bool all_reg = true;             // every instance has FLAG_NE_REG
     int32_t brancher = CSP_BR_FIRST_FAIL;
     std::vector<uint16_t> mlp_params;
     float *logbuf = nullptr;                 // subtree logging (caller-owned device buffers)
@@ -905,7 +924,7 @@ int plan_batch(const csp_batch *b, BatchPlan *P) {
     const bool learned = b->brancher == CSP_BR_LEARNED;
     p.R = record_words(b->nmax * b->W, b->W, b->logbuf ? LOG_EXTRA : 0);
     int rc = make_shape(b->tiling, b->W, p.R, b->depth, b->cons_max, true, learned,
-                        b->logbuf != nullptr, b->nmax, b->ntab_max, &p.shape);
+                        b->logbuf != nullptr, b->nmax, b->ntab_max, b->all_reg, &p.shape);
     if (rc) return rc;
     const Shape &s = p.shape;
     const size_t count = b->hs.size();
@@ -974,7 +993,7 @@ cudaError_t enqueue_batch(csp_batch *b, const SearchArgs &A) {
         e = cudaMemsetAsync(b->ws + b->plan.o_res, 0, b->hs.size() * sizeof(InstResult), b->stream);
     if (e == cudaSuccess) e = launch_init_batch(A, b->plan.shape.blocks, b->stream);
     if (e == cudaSuccess)
-        e = launch_search(b->W, b->plan.shape.stage_words > 0, b->plan.shape.ext, A, b->plan.shape.blocks,
+        e = launch_search(b->W, b->plan.shape.stage_words > 0, b->plan.shape.kind, A, b->plan.shape.blocks,
                           b->plan.shape.warps * 32, b->plan.shape.smem, b->stream);
     return e;
 }
@@ -1012,6 +1031,7 @@ int csp_batch_create(csp_batch_t **out, csp_t *const *hs, int32_t count) {
         b->arena.insert(b->arena.end(), B.begin(), B.end());
         b->cons_max = std::max(b->cons_max, (int)B[H_CONS_WORDS]);
         b->ntab_max = std::max(b->ntab_max, (int)B[H_N_TAB]);
+        b->all_reg = b->all_reg && (B[H_FLAGS] & FLAG_NE_REG) != 0;
         b->sol_off.push_back(sw);
         sw += h->n;
     }
@@ -1041,6 +1061,7 @@ int csp_batch_create_roots(csp_batch_t **out, csp_t *base, int32_t count, const 
     }
     b->cons_max = (int)B[H_CONS_WORDS];
     b->ntab_max = (int)B[H_N_TAB];
+    b->all_reg = (B[H_FLAGS] & FLAG_NE_REG) != 0;
     b->sol_words = (int64_t)n * count;
     *out = b;
     return CSP_OK;
@@ -1144,7 +1165,7 @@ int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph) {
         if (!b->graph || b->graph_mode != b->mode || !same_limits(L, b->graph_lim)) {
             drop_graph(b);
             int bps = 0;   // sets the kernel's shared-memory attribute outside the capture
-            e = occupancy_search(b->W, b->plan.shape.stage_words > 0, b->plan.shape.ext, b->plan.shape.warps * 32,
+            e = occupancy_search(b->W, b->plan.shape.stage_words > 0, b->plan.shape.kind, b->plan.shape.warps * 32,
                                  b->plan.shape.smem, &bps);
             cudaGraph_t g = nullptr;
             if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
@@ -1301,7 +1322,7 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
     if (e == cudaSuccess) e = cudaMemsetAsync(ws + P.o_team, 0, sizeof(Team), st);
     if (e == cudaSuccess) e = launch_init_single(A, st);
     if (e == cudaSuccess)
-        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.ext, A, P.shape.blocks,
+        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.kind, A, P.shape.blocks,
                           P.shape.warps * 32, P.shape.smem, st);
     GState g;
     if (e == cudaSuccess)

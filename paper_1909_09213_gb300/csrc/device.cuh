@@ -400,6 +400,78 @@ __device__ bool fixpoint_ne1(const IV<ST> &I, int dom, int chg, bool full, unsig
     }
 }
 
+// ------------------------------------------------------------------ domains in registers
+// One-word int_ne problems with at most 32 variables (FLAG_NE_REG): lane i of the warp holds
+// D(x_i) in a register (lanes >= n hold 0 and take no part).  A fixed variable v with value
+// bit a removes, from every D(x_i) at once, the bits a + off for the offsets off of the
+// constraints between x_i and x_v: one 8-byte load of the offset mask M(v, i) per lane
+// (consecutive words across the warp) and a funnel shift that aligns bit off + 31 with bit
+// a + off.
+
+// the offset mask of (fixed variable v, variable `lane`): staged or in global memory
+template <bool ST>
+__device__ __forceinline__ uint2 ne_mask(const IV<ST> &I, int nm, int v, int lane) {
+    const int o = nm + 2 * ((v << 5) + lane);
+    if (ST) return *reinterpret_cast<const uint2 *>(&SM[o]);
+    return __ldg(reinterpret_cast<const uint2 *>(I.g + o));
+}
+
+// bits a + off (0 <= a <= 31) of the mask with bit off + 31 per offset: bit b of the result
+// is mask bit b + 31 - a
+__device__ __forceinline__ uint32_t ne_removed(uint2 m, int a) {
+    return __funnelshift_r(m.x, m.y, 31 - a);
+}
+
+// Fixpoint of the node held in registers.  `pending` holds the fixed variables whose
+// consequences have not been applied yet, `done` those whose consequences are already in the
+// domains (the variables fixed in the parent, which is at its fixpoint: its domains contain
+// the child's, so re-applying them would remove nothing).  Each round applies every pending
+// variable's removals (their values are read at the start of the round: a pending variable
+// is fixed, so its domain can only become empty, which fails the node anyway), then the
+// variables newly left with one value become pending.  Returns true when some domain became
+// empty.
+template <bool ST>
+__device__ __forceinline__ bool fixpoint_reg(const IV<ST> &I, uint32_t &d, uint32_t pending,
+                                             uint32_t done, unsigned long long &evals,
+                                             unsigned long long &rounds) {
+    const int lane = lane_id();
+    const bool act = lane < I.n;
+    const int nm = (int)I.w(H_OFF_NEMASK);
+    while (pending) {
+        rounds++;
+        evals += (unsigned)__popc(pending);
+        const int a = __ffs(d) - 1;               // the value of each fixed variable
+        uint32_t rm = 0;
+        uint32_t p = pending;
+        while (p) {                               // two fixed variables per step (independent loads)
+            const int v0 = __ffs(p) - 1;
+            p &= p - 1;
+            const int v1 = p ? __ffs(p) - 1 : v0;
+            p &= p - 1;
+            const int a0 = __shfl_sync(FULLMASK, a, v0);
+            const int a1 = __shfl_sync(FULLMASK, a, v1);
+            const uint2 m0 = ne_mask(I, nm, v0, lane);
+            const uint2 m1 = ne_mask(I, nm, v1, lane);
+            rm |= ne_removed(m0, a0) | ne_removed(m1, a1);
+        }
+        d &= ~rm;
+        done |= pending;
+        if (__any_sync(FULLMASK, act && d == 0u)) return true;
+        pending = __ballot_sync(FULLMASK, act && (d & (d - 1u)) == 0u) & ~done;
+    }
+    return false;
+}
+
+// first-fail over register-held domains: the unfixed variable with the fewest values, lowest
+// index on ties; -1 when every variable is fixed
+__device__ __forceinline__ int select_first_fail_reg(uint32_t d, int n) {
+    const int lane = lane_id();
+    const uint32_t key = (lane < n && (d & (d - 1u))) ? ((uint32_t)__popc(d) << 5) | (uint32_t)lane
+                                                       : 0xffffffffu;
+    const uint32_t best = __reduce_min_sync(FULLMASK, key);
+    return best == 0xffffffffu ? -1 : (int)(best & 31u);
+}
+
 // Propagates the node at SM[dom] (S words) to its fixpoint.  SM[chg] (NW words) holds the
 // variables changed since the last fixpoint; with full = true every variable counts as
 // changed and unary constraints are applied first.  SM[evs] is NW words of scratch.

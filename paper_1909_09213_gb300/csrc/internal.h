@@ -16,7 +16,14 @@ constexpr int MAX_W = 8;                // 256-value window
 constexpr int HDR_WORDS = 32;
 constexpr uint32_t FLAG_TRIVIAL_FAIL = 1u;  // a row with no terms and rhs < 0
 constexpr uint32_t FLAG_NE_ONLY = 2u;       // int_ne constraints only (no lin, alldiff, table)
+constexpr uint32_t FLAG_NE_REG = 4u;        // also one word per domain and n <= 32: the search
+                                            // can hold a node's domains in registers, one
+                                            // variable per lane (offset masks at H_OFF_NEMASK)
 constexpr int WS_WORDS = 92;            // per-warp shared bookkeeping (events, counters)
+// search kernel kinds
+constexpr int KERN_PLAIN = 0;           // first-fail, domains in shared memory
+constexpr int KERN_EXT = 1;             // learned brancher and/or subtree logging
+constexpr int KERN_REG = 2;             // FLAG_NE_REG problems, domains in registers
 
 enum Hdr {
     H_N = 0, H_W, H_LO0, H_S, H_NW, H_FLAGS,
@@ -29,6 +36,7 @@ enum Hdr {
     H_OFF_VFEAT,                      // per variable VFEAT_WORDS words of static feature data
     H_OFF_NB_START, H_OFF_NB,         // neighbour lists: n+1 starts; neighbour indices
     H_MAXDEG,                         // largest constraint degree of a variable
+    H_OFF_NEMASK,                     // FLAG_NE_REG: n x 32 offset masks of 2 words (below)
     H_COUNT
 };
 
@@ -39,6 +47,11 @@ constexpr int VFEAT_WORDS = 8;
 constexpr int N_FEATURES = 16;
 static_assert(H_COUNT <= HDR_WORDS, "header too long");
 
+// int_ne offset masks (FLAG_NE_REG): for a fixed variable v and a variable i, the 64-bit
+// mask at words H_OFF_NEMASK + 2 (32 v + i) (low word first) has bit off + 31 set when some
+// int_ne makes "x_v fixed to bit a" remove bit a + off from D(x_i) (|off| <= 31; larger
+// offsets never meet a one-word domain).  Indexed fixed variable first, so that the 32 lanes
+// of a warp read the masks of one fixed variable from consecutive words.
 // lin row: 3 words (first term, number of terms, rhs); term: 2 words (coef, var)
 // alldiff group: 2 words (first member, number of members)
 // table: 4 words (x, y, word offset of R, word offset of C); R and C hold 32*W rows of W

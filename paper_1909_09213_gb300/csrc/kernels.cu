@@ -15,10 +15,16 @@ CUBICS_DECLARE_WIDTH(1)
 CUBICS_DECLARE_WIDTH(2)
 CUBICS_DECLARE_WIDTH(4)
 CUBICS_DECLARE_WIDTH(8)
+cudaError_t launch_search_reg(bool, const SearchArgs &, int, int, size_t, cudaStream_t);
+cudaError_t occupancy_reg(bool, int, size_t, int *);
 
-// ext: the kernel with the learned brancher and subtree logging
-cudaError_t launch_search(int W, bool staged, bool ext, const SearchArgs &A, int blocks,
+// kind: KERN_PLAIN (first-fail), KERN_EXT (learned brancher and subtree logging) or KERN_REG
+// (one-word int_ne problems with register-held domains; W must be 1)
+cudaError_t launch_search(int W, bool staged, int kind, const SearchArgs &A, int blocks,
                           int threads, size_t smem, cudaStream_t st) {
+    if (kind == KERN_REG)
+        return W == 1 ? launch_search_reg(staged, A, blocks, threads, smem, st) : cudaErrorInvalidValue;
+    const bool ext = kind == KERN_EXT;
 #define CUBICS_CASE(WW)                                                                      \
     case WW:                                                                                 \
         return ext ? launch_search_ext_w##WW(staged, A, blocks, threads, smem, st)           \
@@ -33,7 +39,10 @@ cudaError_t launch_search(int W, bool staged, bool ext, const SearchArgs &A, int
 #undef CUBICS_CASE
 }
 
-cudaError_t occupancy_search(int W, bool staged, bool ext, int threads, size_t smem, int *bps) {
+cudaError_t occupancy_search(int W, bool staged, int kind, int threads, size_t smem, int *bps) {
+    if (kind == KERN_REG)
+        return W == 1 ? occupancy_reg(staged, threads, smem, bps) : cudaErrorInvalidValue;
+    const bool ext = kind == KERN_EXT;
 #define CUBICS_CASE(WW)                                                                      \
     case WW:                                                                                 \
         return ext ? occupancy_ext_w##WW(staged, threads, smem, bps)                         \

@@ -125,9 +125,27 @@ static __device__ bool q_take(uint32_t *seq, uint32_t *rec, uint32_t t, int dst,
 #ifndef CUBICS_SMALL_NS_BATCH
 #define CUBICS_SMALL_NS_BATCH 30000.f
 #endif
+// The same for the register-held kernel's single-problem queue: its nodes are ~3x shorter,
+// and passing small records on merely churns the queue at the end of the search (measured
+// on 16-queens: 2.2 G nodes/s at 80 us, 2.6 G at 320 - 1280 us, 2.3 G at 2.56 ms)
+#ifndef CUBICS_SMALL_NS_GRID_REG
+#define CUBICS_SMALL_NS_GRID_REG 640000.f
+#endif
 // records observed in a bin before its statistics are trusted
 #ifndef CUBICS_USTAT_MIN
 #define CUBICS_USTAT_MIN 8u
+#endif
+
+// while workers wait for records, a busy worker checks the donation signal every this many
+// nodes (every 8th node otherwise)
+#ifndef CUBICS_HUNGRY_EVERY
+#define CUBICS_HUNGRY_EVERY 4u
+#endif
+
+// nodes between two reads of the stop flags by a worker whose nodes are held in registers
+// (its nodes are short: a read per node would wait on a global load every node)
+#ifndef CUBICS_POLL_EVERY
+#define CUBICS_POLL_EVERY 16u
 #endif
 
 // most records one donation check may push
@@ -139,7 +157,10 @@ static __device__ bool q_take(uint32_t *seq, uint32_t *rec, uint32_t t, int dst,
 
 // EXT: the worker can run the learned brancher and subtree logging.  Without them the
 // search compiles into a separate kernel that fits in fewer registers (more resident warps).
-template <int W, bool ST, bool EXT>
+// REG: one-word int_ne problems with at most 32 variables (FLAG_NE_REG); a node's domains are
+// propagated and labelled in registers, one variable per lane, and reach shared memory only
+// when the node opens a search level (records keep the layout of the other kernels).
+template <int W, bool ST, bool EXT, bool REG = false>
 struct Worker {
     IV<ST> I;
     Team *T;
@@ -149,6 +170,8 @@ struct Worker {
     int top, base;        // open levels [0, top); levels >= base are in shared memory
     uint32_t tick;        // nodes of this worker (low bits pace the periodic checks)
     int hungry;           // the last donation check saw workers waiting for records
+    uint32_t worth_bins;  // bit b: records of size bin b are worth passing on (refreshed with
+                          // the limits, every 64 nodes, from the team's subtree statistics)
     uint32_t taken;       // tick when the current record was taken
     int pbin;             // size-statistics bin of the current record
     uint32_t credited;    // tick up to which its nodes were added to the bin
@@ -206,7 +229,8 @@ struct Worker {
 
     // Node and time limits, every 64 nodes.  In batch mode the node limit is per instance:
     // the team's instance stops (found = 2) and the others go on.
-    __device__ void check_limits() {
+    __device__ __noinline__ void check_limits() {
+        refresh_worth();
         if (lane_id() == 0) {
             atomicAdd(&T->usum[pbin], (unsigned long long)(tick - credited));
             credited = tick;
@@ -225,6 +249,26 @@ struct Worker {
                 atomicExch(&SA.g->abort, 1);
             }
         }
+    }
+
+    // Which size bins are worth donating: a bin's records took, on average, its mean nodes
+    // times the team's mean time per node; bins with too few records observed count as
+    // worth it.  One lane per bin.
+    __device__ void refresh_worth() {
+        const int lane = lane_id();
+        const uint32_t cnt = ld_volatile(&T->ucnt[lane]);
+        const unsigned long long sum = ld_volatile(&T->usum[lane]);
+        const unsigned long long xn = ld_volatile(&T->xnodes);
+        const unsigned long long xs = ld_volatile(&T->xns);
+        bool w = true;
+        if (cnt >= CUBICS_USTAT_MIN && xn > 0) {
+            const float mean_nodes = (float)sum / (float)cnt;
+            const float node_ns = (float)xs / (float)xn;
+            const float thr = SA.batch ? CUBICS_SMALL_NS_BATCH
+                                       : (REG ? CUBICS_SMALL_NS_GRID_REG : CUBICS_SMALL_NS_GRID);
+            w = mean_nodes * node_ns >= thr;
+        }
+        worth_bins = __ballot_sync(FULLMASK, w);
     }
 
     __device__ void record_solution(int st) {
@@ -265,6 +309,45 @@ struct Worker {
         __syncwarp();
     }
 
+    // record_solution for a node held in registers (lane i: the one value of x_i)
+    __device__ __noinline__ void record_solution_reg(uint32_t d) {
+        const int lane = lane_id();
+        const int n = I.n;
+        bool keep = true;
+        if (SA.mode == 1) {
+            int won = 0;
+            if (lane == 0) won = atomicCAS(&T->found, 0, 1) == 0;
+            keep = __shfl_sync(FULLMASK, won, 0) != 0;
+            stop = 1;
+        }
+        if (!keep) return;
+        const int val = I.lo0 + __ffs(d) - 1;
+        unsigned long long h = 0x9E3779B97F4A7C15ull;
+        for (int i = 0; i < n; ++i) {
+            const unsigned vi = (unsigned)__shfl_sync(FULLMASK, val, i);
+            h = splitmix64(h ^ (((unsigned long long)(unsigned)i << 32) | vi));
+        }
+        if (lane == 0) {
+            WarpShared &w = ws();
+            w.sols++;
+            w.hsum += h;
+            w.hxor ^= h;
+            if (SA.batch) atomicAdd(&SA.results[inst].solutions, 1ull);
+        }
+        long long slot_off = -1;
+        if (SA.mode == 1) {
+            slot_off = ws().sol_off;
+        } else if (SA.cap > 0) {
+            unsigned long long s = 0;
+            if (lane == 0 && ld_volatile((const uint32_t *)&SA.g->stored) < (uint32_t)SA.cap)
+                s = atomicAdd(&SA.g->stored, 1ull) + 1ull;
+            s = __shfl_sync(FULLMASK, s, 0);
+            if (s > 0 && (long long)s <= SA.cap) slot_off = (long long)(s - 1) * n;
+        }
+        if (slot_off >= 0 && SA.sols != nullptr && lane < n) SA.sols[slot_off + lane] = val;
+        __syncwarp();
+    }
+
     // unfixed variables of the record at SM offset `Ls` (>= 0) or global `Lg` (every lane)
     __device__ int count_unfixed(int Ls, const uint32_t *Lg) const {
         int c = 0;
@@ -285,7 +368,7 @@ struct Worker {
     // being expanded keeps its lowest value.  A level is not given away when the records
     // with its share of unfixed variables taken so far took little time on average; the
     // levels below it are smaller still, so the donation ends there.
-    __device__ void donate(int most) {
+    __device__ __noinline__ void donate(int most) {
         const int lane = lane_id();
         for (int s = 0; s < top; ++s) {
             const bool in_sm = s >= base;
@@ -300,21 +383,9 @@ struct Worker {
                 pc -= nz ? 1 : 0;
             }
             if (pc == 0) continue;
+            // the size bin's worth, from the statistics last read (refresh_worth)
             const int u = count_unfixed(Ls, Lg);
-            int worth = 1;
-            if (lane == 0) {
-                // average time of a record from this bin: its mean nodes times the team's
-                // mean time per node (nodes differ in cost from one problem to another)
-                const uint32_t cnt = ld_volatile(&T->ucnt[ubin(u)]);
-                const unsigned long long xn = ld_volatile(&T->xnodes);
-                if (cnt >= CUBICS_USTAT_MIN && xn > 0) {
-                    const float mean_nodes = (float)ld_volatile(&T->usum[ubin(u)]) / (float)cnt;
-                    const float node_ns = (float)ld_volatile(&T->xns) / (float)xn;
-                    worth = mean_nodes * node_ns >=
-                            (SA.batch ? CUBICS_SMALL_NS_BATCH : CUBICS_SMALL_NS_GRID);
-                }
-            }
-            if (!__shfl_sync(FULLMASK, worth, 0)) return;
+            if (!((worth_bins >> ubin(u)) & 1u)) return;
             int budget = 0;
             if (lane == 0) {
                 const int k = min(most, pc);
@@ -500,7 +571,7 @@ struct Worker {
         uint32_t p_head = 0, p_prom = 0;
         // every 8th node; every node while workers are starved (ramp-up and the tail); never
         // in the first nodes of a record, so that small subtrees are not passed on
-        const bool may_donate = !(SA.flags & F_NO_DONATE) && (hungry || (tick & 7) == 0) &&
+        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? CUBICS_HUNGRY_EVERY - 1u : 7u)) == 0u) &&
                                 tick - taken >= CUBICS_DONATE_AFTER;
         if (may_donate && lane == 0) {
             p_head = ld_volatile(&T->head);
@@ -575,9 +646,124 @@ struct Worker {
         }
     }
 
+    // node() for a node held in registers: d is lane i's D(x_i), `pending` the fixed
+    // variables not yet propagated, `done` the ones already propagated (full: the record's
+    // root node, whose unary constraints and fixed variables are all still to apply).  On
+    // success the node opens level cl in its shared slot.
+    __device__ void node_reg(uint32_t d, int cl, uint32_t pending, uint32_t done, bool full) {
+        const int lane = lane_id();
+        const int n = I.n;
+        tick++;
+        const bool polled = full || (tick & (CUBICS_POLL_EVERY - 1u)) == 0u;
+        const int p_stop = polled ? poll() : 0;
+        uint32_t p_head = 0, p_prom = 0;
+        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? CUBICS_HUNGRY_EVERY - 1u : 7u)) == 0u) &&
+                                tick - taken >= CUBICS_DONATE_AFTER;
+        if (may_donate && lane == 0) {
+            p_head = ld_volatile(&T->head);
+            p_prom = ld_volatile(&T->promised);
+        }
+        if ((tick & 63) == 0) check_limits();
+        unsigned long long ev = 0, rnd = 0;
+        bool failed = false;
+        if (full) {
+            const int nun = (int)I.w(H_N_UN), un = (int)I.w(H_OFF_UN);
+            for (int k = 0; k < nun; ++k) {
+                const uint32_t u = I.w(un + k);
+                if ((int)(u & 0xffffu) == lane) d &= ~(1u << (u >> 16));
+            }
+            failed = __any_sync(FULLMASK, lane < n && d == 0u);
+            pending = __ballot_sync(FULLMASK, lane < n && (d & (d - 1u)) == 0u);
+        }
+        if (!failed) failed = fixpoint_reg<ST>(I, d, pending, full ? 0u : done, ev, rnd);
+        const bool split_root = full && !SA.batch && SA.nparts > 1;
+        const bool counted = !split_root || SA.part == 0;
+        if (lane == 0 && counted) {
+            WarpShared &w = ws();
+            w.nodes++;
+            w.evals += ev;
+            w.rounds += rnd;
+        }
+        if (polled) stop = __shfl_sync(FULLMASK, p_stop, 0);
+        if (failed) {
+            if (lane == 0 && counted) ws().fails++;
+            refill();
+            return;
+        }
+        const int y = select_first_fail_reg(d, n);
+        if (y < 0) {
+            if (counted) record_solution_reg(d);
+            refill();
+            return;
+        }
+        uint32_t rw = __shfl_sync(FULLMASK, d, y);
+        if (split_root) {
+            // keep the values whose position in D(y), ascending, is part mod nparts
+            uint32_t keep = 0;
+            for (uint32_t m = rw; m; m &= m - 1) {
+                const uint32_t bit = m & (~m + 1u);
+                if ((uint32_t)__popc(rw & (bit - 1u)) % (uint32_t)SA.nparts == (uint32_t)SA.part) keep |= bit;
+            }
+            rw = keep;
+        }
+        const int C = slot(cl);
+        if (lane < n) SM[C + lane] = d;
+        if (lane == 0) {
+            SM[C + S] = rw;
+            SM[C + S + 1] = (uint32_t)y;
+        }
+        __syncwarp();
+        top = cl + 1;
+        if (lane == 0 && top > ws().maxd) ws().maxd = top;
+        if (may_donate) {
+            const int owed = max((int)(p_head - p_prom), 0);
+            const int want = __shfl_sync(FULLMASK, min(owed, CUBICS_DONATE_MAX), 0);
+            hungry = want > 0;
+            if (want > 0) donate(want);
+        }
+    }
+
+    // expand() for register-held nodes: the parent's domains go straight into registers; only
+    // a child that opens a level is written back
+    __device__ void expand_reg() {
+        const int lane = lane_id();
+        const int p = top - 1;
+        const int P = slot(p);
+        const uint32_t r = SM[P + S];
+        if (!r) {
+            top = p;
+            refill();
+            return;
+        }
+        const int v = __ffs(r) - 1;
+        const uint32_t rest = r & (r - 1u);
+        const int x = (int)SM[P + S + 1];
+        uint32_t d = lane < I.n ? SM[P + lane] : 0u;
+        // the parent is at its fixpoint: its fixed variables' consequences are in d already
+        const uint32_t done = __ballot_sync(FULLMASK, lane < I.n && (d & (d - 1u)) == 0u);
+        if (lane == x) d = 1u << v;
+        __syncwarp();
+        int cl;
+        if (rest == 0u) {                 // the last value: the level's slot becomes the child's
+            cl = p;
+            top = p;
+        } else {
+            if (lane == 0) SM[P + S] = rest;
+            cl = p + 1;
+            make_room(cl);
+        }
+        __syncwarp();
+        node_reg(d, cl, 1u << x, done, false);
+    }
+
     // child of the top level: next value of its branching variable (the level is popped
     // when it has none left)
     __device__ void expand() {
+        if constexpr (REG) expand_reg();
+        else expand_copy();
+    }
+
+    __device__ void expand_copy() {
         const int lane = lane_id();
         const int p = top - 1;
         const int P = slot(p);
@@ -625,8 +811,12 @@ struct Worker {
         stop = __shfl_sync(FULLMASK, poll(), 0);
         if (stop) return;
         const int var = (int)SM[slots + S + W];
-        if (var < 0) node(slots, 0, true);
-        else top = 1;
+        if (var < 0) {
+            if constexpr (REG) node_reg(lane_id() < I.n ? SM[slots + lane_id()] : 0u, 0, 0u, 0u, true);
+            else node(slots, 0, true);
+        } else {
+            top = 1;
+        }
         while (top > 0) {
             if (stop) { top = 0; break; }
             expand();
@@ -724,7 +914,7 @@ __device__ __forceinline__ void stage_instance(const uint32_t *ib) {
     for (int i = threadIdx.x; i < words / 4; i += blockDim.x) d[i] = s[i];
 }
 
-template <int W, bool ST, bool EXT>
+template <int W, bool ST, bool EXT, bool REG = false>
 __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     __shared__ int s_inst, s_team;
@@ -736,13 +926,14 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
         __syncthreads();
     }
 
-    Worker<W, ST, EXT> wk;
+    Worker<W, ST, EXT, REG> wk;
     wk.lsm = SA.lsm;
     wk.slots = SA.warp_base + warp * per_warp;
     wk.wso = wk.slots + SA.lsm * SA.rmax;
     wk.gw = blockIdx.x * SA.warps + warp;
     wk.tick = 0;
     wk.hungry = 1;                   // the first nodes feed the idle workers at once
+    wk.worth_bins = 0xffffffffu;     // nothing observed yet: every size is worth passing on
     wk.taken = 0;
     wk.pbin = 0;
     wk.credited = 0;
@@ -804,6 +995,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
         wk.S = wk.I.S;
         wk.R = record_words(wk.S, W, SA.log_extra);
         wk.T = T;
+        wk.worth_bins = 0xffffffffu;     // another team: its statistics are read at the next check
         wk.team = team;
         wk.inst = i;
         const unsigned long long n0 = wk.ws().nodes, f0 = wk.ws().fails;
@@ -882,6 +1074,15 @@ __global__ void __launch_bounds__(512, 1) search_kernel_ext(const SearchArgs Ap)
     search_body<W, ST, true>(Ap);
 }
 
+// one-word int_ne problems of at most 32 variables, domains in registers (FLAG_NE_REG)
+#ifndef CUBICS_REGS_REG
+#define CUBICS_REGS_REG 64
+#endif
+template <bool ST>
+__global__ void __maxnreg__(CUBICS_REGS_REG) search_kernel_reg(const SearchArgs Ap) {
+    search_body<1, ST, false, true>(Ap);
+}
+
 // ------------------------------------------------------------------ propagate kernel
 
 template <int W, bool ST>
@@ -934,6 +1135,17 @@ cudaError_t occupancy_k(K kern, int threads, size_t smem, int *bps) {
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kern, threads, smem);
 }
+
+#define CUBICS_DEFINE_REG                                                                    \
+    cudaError_t launch_search_reg(bool st_, const SearchArgs &A, int b, int t, size_t sm,     \
+                                  cudaStream_t s) {                                         \
+        return st_ ? launch_k(search_kernel_reg<true>, A, b, t, sm, s)                      \
+                   : launch_k(search_kernel_reg<false>, A, b, t, sm, s);                    \
+    }                                                                                       \
+    cudaError_t occupancy_reg(bool st_, int t, size_t sm, int *bps) {                       \
+        return st_ ? occupancy_k(search_kernel_reg<true>, t, sm, bps)                       \
+                   : occupancy_k(search_kernel_reg<false>, t, sm, bps);                     \
+    }
 
 template <int W, bool ST, bool EXT>
 cudaError_t launch_search_t(const SearchArgs &A, int blocks, int threads, size_t smem,

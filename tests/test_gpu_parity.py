@@ -248,6 +248,51 @@ def test_search_every_kind_wide_domains(span, W):
         search_parity(m, TILINGS["spilling"], cap=0)
 
 
+def random_ne_model(seed, n, dmax, m):
+    """One-word int_ne-only problems: domains of up to dmax values (holes included) inside
+    one 32-value window, binary constraints with offsets up to +-40 (beyond one word as
+    well), unary ones, and self constraints x != x + c."""
+    s = I.Stream(seed)
+    lo0 = int(s.int(-5, 5))
+    lo, hi = [], []
+    for i in range(n):
+        a = lo0 + int(s.int(0, 31 - dmax))
+        lo.append(a)
+        hi.append(a + int(s.int(1, dmax - 1)))
+    M = I.CspModel(n=n, lo=lo, hi=hi, name=f"ne-{n}-{seed}")
+    for i in range(n):
+        if s.int(0, 3) == 0:
+            M.removed.append((i, int(s.int(lo[i], hi[i]))))
+    for _ in range(m):
+        x, k = int(s.int(0, n - 1)), int(s.int(0, 19))
+        if k == 0:
+            M.ne.append((x, -1, int(s.int(lo0, lo0 + 31))))
+        elif k == 1:
+            M.ne.append((x, x, int(s.int(-2, 2))))
+        elif k == 2:
+            M.ne.append((x, x, int(s.int(1, 3))))
+        else:
+            y = int(s.int(0, n - 1))
+            M.ne.append((x, y, int(s.int(-40, 40)) if k < 6 else int(s.int(-6, 6))))
+    return M
+
+
+@pytest.mark.parametrize("n,dmax,m", [(6, 8, 12), (12, 6, 30), (20, 5, 70), (32, 3, 110), (33, 3, 110)])
+def test_search_random_ne_one_word(n, dmax, m):
+    """The register-held kernel (n <= 32) and the shared-memory one (n = 33) on random
+    int_ne models that the oracle decides within 200 000 nodes."""
+    compared, big = 0, 0
+    for seed in range(40):
+        M = random_ne_model(500 + 7 * seed + n, n, dmax, m)
+        r = O.solve(O.OracleModel(M), cap=0, variant=1, node_limit=200_000)
+        if r.status < 0:
+            continue
+        search_parity(M, cap=2000)
+        compared += 1
+        big += r.nodes >= 1000
+    assert compared >= 10 and big >= 2, (compared, big)
+
+
 def test_search_spill_heavy_deep_stack():
     # 12-queens with 2 shared-memory levels per worker: most levels live in global memory
     st = search_parity(I.queens(12), K.tiling(blocks=4, warps_per_block=8, smem_levels=2), cap=10)
@@ -386,16 +431,21 @@ def test_failed_upload_leaves_the_previous_upload_usable():
 
 
 def test_block_beyond_register_budget_is_einval():
-    # the first-fail kernel is capped below 64 K / 1024 registers per thread: a 32-warp block
-    # does not fit, a 16-warp block does
-    p = K.Csp(I.queens(8))
+    # the one-word first-fail kernel is capped at 80 registers per thread: a 32-warp block
+    # (32 x 32 x 80 > 64 K registers) does not fit, a 16-warp block does
+    m = I.model_rb(I.seed_for(I.CFG_RB, 5), 14, 6)
+    p = K.Csp(m)
     p.set_tiling(K.tiling(warps_per_block=32))
     with pytest.raises(K.CspError) as e:
         p.workspace_bytes(K.CSP_ALL, 0)
     assert e.value.code == K.CSP_EINVAL
     p.set_tiling(K.tiling(warps_per_block=16))
+    search_parity(m, K.tiling(warps_per_block=16))
+    # the register-held int_ne kernel (64 registers) takes a whole 32-warp block
+    p = K.Csp(I.queens(8))
+    p.set_tiling(K.tiling(warps_per_block=32))
     rc, st, _ = p.solve(K.CSP_ALL, 0)
-    assert rc == 0 and st["solutions"] == queens_count(8)
+    assert rc == 0 and st["solutions"] == queens_count(8) and st["workers"] % 32 == 0
 
 
 # ----------------------------------------------------------------------------- batches
