@@ -4,15 +4,24 @@
 A step is one complete search of the workload (every node labelled, propagated to its
 fixpoint and backtracked on the GPU).  Workloads:
 
-* queens16 (default) / queens14: N-queens, all solutions (N vars, 3 C(N,2) int_ne, one uint32
-  word per domain), one problem per step;
+* queens16 (default) / queens15 / queens14: N-queens, all solutions (N vars, 3 C(N,2) int_ne,
+  one uint32 word per domain), one problem per step;
 * rb4096: 4096 seeded model-RB instances (n ~ U[20,60], d ~ U[8,32], tables), first solution
   or UNSAT proof for each, all in one persistent launch replayed from a CUDA graph, with the
-  launch shape chosen by the autotuner.
+  launch shape chosen by the autotuner;
+* linad256: 256 mixed linear/alldifferent instances (200 vars on 0..255), first solution;
+* rb_learned: 1024 held-out model-RB instances (n = 80, d = 20) with the learned brancher,
+  trained first on subtree logs of 20 000 exhaustive searches, against first-fail;
+* lns: one round of parallel large neighbourhood search on a mixed instance.
+
+With the default workload the batch workloads also run once, after the timed steps, and are
+reported under config.secondary: verdicts against the oracle, per-instance time to solution,
+batched against one-at-a-time first-fail search, learned against first-fail ordering.  The
+CPU baseline is the oracle on one host core and, for N-queens, on every host core.
 
 Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload queens16|queens14|rb4096]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--no-secondary]
   python bench.py --impl reference      # the CPU oracle on a bounded sample of the workload
 
 Multi-GPU (torchrun): every rank solves its own copy of the workload (independent
@@ -124,6 +133,76 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workloads
 
+def _time_to_solution(res):
+    """median / p90 / max of the instances' own search times (csp_result.ms), by verdict"""
+    out = {}
+    for name, sel in (("", lambda r: True), ("_sat", lambda r: r["status"] == 1),
+                      ("_unsat", lambda r: r["status"] == 0)):
+        ms = sorted(r["ms"] for r in res if sel(r))
+        if ms:
+            out[f"time_to_solution_ms{name}"] = {
+                "median": float(np.median(ms)), "p90": float(np.percentile(ms, 90)),
+                "max": float(ms[-1])}
+    return out
+
+
+def cpu_description():
+    """host CPU model and core count (lscpu where it exists)"""
+    model = ""
+    try:
+        for ln in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def _queens_subtree_nodes(args):
+    """pool worker: the oracle's all-solution search of the N-queens subtree below `prefix`
+    (x_0 .. x_{k-1} fixed); returns its node count"""
+    N, prefix = args
+    from oracle import oracle as O
+    from paper_1909_09213_gb300 import instances as I
+    m = I.queens(N)
+    for v, a in enumerate(prefix):
+        m.removed += [(v, u) for u in range(N) if u != a]
+    return O.solve(O.OracleModel(m), variant=1, W=1).nodes
+
+
+def queens_oracle_all_cores(N, budget_s=15.0):
+    """The oracle as it stands, run on every host core at once over N-queens subtrees with
+    x_0, x_1, x_2 fixed (queens-consistent prefixes in lexicographic order), one subtree per
+    process, until about budget_s of wall time has passed.  A spawn pool, so that no process
+    is forked from one that holds a CUDA context."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    prefixes = [(a, b, c) for a in range(N) for b in range(N) for c in range(N)
+                if a != b and b != c and a != c and abs(a - b) != 1 and abs(b - c) != 1
+                and abs(a - c) != 2]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_queens_subtree_nodes, [(6, (0,))] * cores)       # start-up, untimed
+        t = time.perf_counter()
+        nodes, k, dt = 0, 0, 0.0
+        # subtrees are fed one at a time to whichever process is free; counted until the
+        # budget is spent (the ones still running then are dropped, their time included)
+        for c in pool.imap_unordered(_queens_subtree_nodes, [(N, p) for p in prefixes]):
+            nodes += c
+            k += 1
+            dt = time.perf_counter() - t
+            if dt >= budget_s:
+                break
+        pool.terminate()
+    return {"value": nodes / dt, "unit": "nodes/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{N}-queens subtrees with x0, x1, x2 fixed, consistent prefixes in "
+                       f"lexicographic order fed to {cores} processes: {k} finished "
+                       f"({nodes} nodes, {dt:.1f} s wall)")}
+
+
 class Queens:
     """N-queens, all solutions: one problem per step."""
 
@@ -134,6 +213,8 @@ class Queens:
         self.desc = (f"{N}-queens, all solutions ({N} vars, {len(self.model.ne)} int_ne, "
                      "1 uint32 word per domain)")
         self.profile = f"search_kernel_queens{N}.md"
+        # one-word int_ne problems of at most 32 variables: domains held in registers
+        self.kernel = "search_kernel_reg<true>" if N <= 32 else "search_kernel<1, true>"
 
     def golden(self):
         path = os.path.join(GOLDEN, "queens_oracle.txt")
@@ -211,6 +292,7 @@ class RBBatch:
         self.desc = (f"{count} model-RB instances, n~U[20,60], d~U[8,32], alpha 0.8, r 0.7, "
                      f"p {I.rb_tightness():.6f}, first solution or UNSAT each, one launch (CUDA graph)")
         self.profile = "search_kernel_rb4096.md"
+        self.kernel = "search_kernel<1, true>"
 
     def golden(self):
         path = os.path.join(GOLDEN, "rb4096_oracle.txt")
@@ -312,6 +394,44 @@ class RBBatch:
         out["batched_gpu_kernel_ms_sample512"] = b.stats()["ms"]
         return out
 
+    def secondary(self, K, stream):
+        """One batched launch of the whole workload, as a secondary line of the default run:
+        verdicts against the oracle's file, per-instance time to solution, the node count
+        against the oracle's sequential search, and plain one-at-a-time first-fail search."""
+        t0 = time.time()
+        self.setup(K, stream)
+        setup_s = time.time() - t0
+        self.collect(K)
+        st = self.b.stats()
+        res = self.res
+        nodes = sum(r["nodes"] for r in res)
+        out = {"workload": self.desc, "setup_s": round(setup_s, 1),
+               "tiling": {f: getattr(self.tiling, f) for f, _ in K.csp_tiling._fields_},
+               "launch_ms": st["ms"], "nodes": nodes, "nodes_per_s": nodes / (st["ms"] * 1e-3),
+               "sat": sum(r["status"] == 1 for r in res), "unsat": sum(r["status"] == 0 for r in res),
+               "undecided": sum(r["status"] < 0 for r in res)}
+        out.update(_time_to_solution(res))
+        out.update(self._oracle_comparison(res))
+        out.update(self.extra(K, st))                  # before parity: it may set references
+        out["parity_with_oracle_reference"] = self.parity(st)
+        return out
+
+    def _oracle_comparison(self, res):
+        """verdicts against the oracle's file, and nodes against its sequential first-solution
+        search, on the instances the oracle decided within its node budget"""
+        g = self.golden()
+        if g is None:
+            return {}
+        dec = [(r, g[i]) for i, r in enumerate(res) if g[i][0] >= 0]
+        mism = sum(r["status"] != s for r, (s, _) in dec)
+        out = {"oracle_decided": len(dec), "verdict_mismatches": mism}
+        for name, sel in (("all", lambda s: True), ("sat", lambda s: s == 1), ("unsat", lambda s: s == 0)):
+            pairs = [(r["nodes"], n) for r, (s, n) in dec if sel(s)]
+            if pairs:
+                out[f"gpu_over_oracle_nodes_{name}"] = sum(a for a, _ in pairs) / max(1, sum(b for _, b in pairs))
+                out[f"gpu_over_oracle_nodes_{name}_median"] = float(np.median([a / max(b, 1) for a, b in pairs]))
+        return out
+
     def _oracle_instances(self, start, budget_s, node_limit=100_000):
         from oracle import oracle as O
         nodes, secs, k = 0, 0.0, start
@@ -345,6 +465,7 @@ class LearnedRB(RBBatch):
         self.desc = (f"{eval_count} held-out model-RB instances n=80, d=20, first solution, learned "
                      f"brancher trained on {train_count} exhaustive searches (n=30, d=16)")
         self.profile = "search_kernel_rb_learned.md"
+        self.kernel = "search_kernel_ext<1, true>"
 
     def golden(self):
         return None
@@ -427,6 +548,7 @@ class LinAdBatch(RBBatch):
                      f"5-20 terms, 20 alldifferent groups of 10, rhs theta {I.LINAD_THETA}, first "
                      f"solution, {self.NODE_LIMIT} nodes at most per instance")
         self.profile = "search_kernel_linad256.md"
+        self.kernel = "search_kernel<8, false>"
 
     def golden(self):
         return None
@@ -506,6 +628,7 @@ class LNSRound(RBBatch):
                      f"{self.COPIES} neighbourhoods, {self.FRAC:.0%} of the vars reset, "
                      f"{self.NODE_LIMIT} nodes at most each, first solution, one launch (CUDA graph)")
         self.profile = "search_kernel_lns_linad.md"
+        self.kernel = "search_kernel<8, false>"
 
     def golden(self):
         return None
@@ -761,18 +884,33 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
                 "frac": achieved / smem_peak, "traffic": traffic_from_profile(wl.profile),
                 "peak_source": "measured: csp_probe_smem_bandwidth (volatile 128-bit ld.shared, all SMs)",
-                "bytes_per_node": bpn, "kernel": "search_kernel<1, true>", "kernel_ms": kernel_ms}
+                "bytes_per_node": bpn, "kernel": wl.kernel, "kernel_ms": kernel_ms}
     cpu = None
     if not args.no_cpu_baseline:
         n_s, dt, sample = wl.cpu_sample()
         cpu = {"value": n_s / dt, "unit": "nodes/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample} ({n_s} nodes, {dt:.1f} s on one host core)"}
+        cpu.update(cpu_description())
+        if isinstance(wl, Queens):
+            note("oracle on every host core")
+            cpu["all_cores"] = queens_oracle_all_cores(wl.N)
+    secondary = None
+    if args.secondary and world == 1 and args.workload == "queens16":
+        secondary = {}
+        for name, make in (("rb4096", lambda: RBBatch(4096)), ("linad256", lambda: LinAdBatch(256)),
+                           ("rb_learned", lambda: LearnedRB())):
+            note(f"secondary workload {name}")
+            t0 = time.time()
+            secondary[name] = make().secondary(K, stream)
+            secondary[name]["wall_s"] = round(time.time() - t0, 1)
     config = {"workload": wl.desc, "nodes_per_step": st["nodes"],
               "l2": "flushed before every step (256 MiB write, untimed)",
               "workers": st["workers"], "blocks": st["blocks"],
               "idle_fraction": st["wait_ns"] / max(1.0, st["workers"] * kernel_ms * 1e6),
               "parity_with_oracle_reference": parity}
     config.update(extra)
+    if secondary is not None:
+        config["secondary"] = secondary
     line = {"metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
@@ -791,6 +929,11 @@ def main():
                     choices=["queens16", "queens15", "queens14", "rb4096", "rb_learned", "linad256",
                              "lns"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--secondary", dest="secondary", action="store_true", default=True,
+                    help="with the default workload: also run the batch workloads once "
+                         "(model RB, mixed linear/alldifferent, learned branching) and report "
+                         "them under config.secondary")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -102,6 +102,8 @@ typedef struct {
     uint64_t fails;
     uint64_t solutions;      /* CSP_ALL: every solution; CSP_FIRST: 1 when SAT */
     int64_t sol_offset;      /* first solution of the instance: values at sol + sol_offset */
+    double ms;               /* device time from the start of the instance's search (its block
+                                took it) to its verdict */
 } csp_result;
 
 /* ---------------------------------------------------------------- model (host only) */

@@ -1214,6 +1214,7 @@ int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol) {
             out[i].fails = res[i].fails;
             out[i].solutions = res[i].solutions;
             out[i].sol_offset = b->sol_off[i];
+            out[i].ms = res[i].t_end > res[i].t_start ? 1e-6 * (double)(res[i].t_end - res[i].t_start) : 0.0;
         }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);

@@ -108,6 +108,8 @@ struct InstResult {
     int32_t n;
     unsigned long long nodes, fails, solutions;
     int64_t sol_offset;
+    long long t_start, t_end; // global timer (ns) when the owning block started the instance and
+                              // when its verdict became final
 };
 
 struct SearchArgs {

@@ -125,12 +125,24 @@ static __device__ bool q_take(uint32_t *seq, uint32_t *rec, uint32_t t, int dst,
 #ifndef CUBICS_SMALL_NS_BATCH
 #define CUBICS_SMALL_NS_BATCH 30000.f
 #endif
-// The same for the register-held kernel's single-problem queue: its nodes are ~3x shorter,
-// and passing small records on merely churns the queue at the end of the search (measured
-// on 16-queens: 2.2 G nodes/s at 80 us, 2.6 G at 320 - 1280 us, 2.3 G at 2.56 ms)
+// The same for the register-held kernel's single-problem queue.  Its nodes are ~3x shorter,
+// and every record passed costs ~10 global atomics on the few counters of the team, so that
+// many small records make the whole grid wait on those addresses (measured with 4864
+// workers: 16-queens 0.9 G nodes/s at 160 us, 3.3 G at 640 us, 3.2 G at 1.28 ms; 15-queens
+// 0.6 G at 640 us, 1.7 G at 1.28 ms)
 #ifndef CUBICS_SMALL_NS_GRID_REG
-#define CUBICS_SMALL_NS_GRID_REG 640000.f
+#define CUBICS_SMALL_NS_GRID_REG 1280000.f
 #endif
+#ifndef CUBICS_REG_THR_FLOOR
+#define CUBICS_REG_THR_FLOOR 0.0625f
+#endif
+// 1: a size bin's statistics count only finished records (a record still running is no
+// evidence that its bin is small, so the first levels of a search are passed on at once);
+// 0: running records are credited the nodes explored so far
+#ifndef CUBICS_FINISHED_STATS
+#define CUBICS_FINISHED_STATS 1
+#endif
+
 // records observed in a bin before its statistics are trusted
 #ifndef CUBICS_USTAT_MIN
 #define CUBICS_USTAT_MIN 8u
@@ -172,6 +184,7 @@ struct Worker {
     int hungry;           // the last donation check saw workers waiting for records
     uint32_t worth_bins;  // bit b: records of size bin b are worth passing on (refreshed with
                           // the limits, every 64 nodes, from the team's subtree statistics)
+    int owed_seen;        // workers waiting for a record at the last donation check
     uint32_t taken;       // tick when the current record was taken
     int pbin;             // size-statistics bin of the current record
     uint32_t credited;    // tick up to which its nodes were added to the bin
@@ -232,8 +245,10 @@ struct Worker {
     __device__ __noinline__ void check_limits() {
         refresh_worth();
         if (lane_id() == 0) {
-            atomicAdd(&T->usum[pbin], (unsigned long long)(tick - credited));
-            credited = tick;
+            if (!CUBICS_FINISHED_STATS) {
+                atomicAdd(&T->usum[pbin], (unsigned long long)(tick - credited));
+                credited = tick;
+            }
             if (SA.node_limit > 0 && SA.batch) {
                 const unsigned long long tot = atomicAdd(&T->progress, 64ull) + 64ull;
                 if ((long long)tot >= SA.node_limit) atomicCAS(&T->found, 0, 2);
@@ -264,8 +279,14 @@ struct Worker {
         if (cnt >= CUBICS_USTAT_MIN && xn > 0) {
             const float mean_nodes = (float)sum / (float)cnt;
             const float node_ns = (float)xs / (float)xn;
-            const float thr = SA.batch ? CUBICS_SMALL_NS_BATCH
-                                       : (REG ? CUBICS_SMALL_NS_GRID_REG : CUBICS_SMALL_NS_GRID);
+            float thr = SA.batch ? CUBICS_SMALL_NS_BATCH
+                                 : (REG ? CUBICS_SMALL_NS_GRID_REG : CUBICS_SMALL_NS_GRID);
+            if (REG && !SA.batch) {
+                // the more workers wait, the smaller the records worth passing on: a waiting
+                // worker's time is lost anyway (down to CUBICS_REG_THR_FLOOR of the threshold)
+                const float busy = 1.f - (float)owed_seen / (float)(gridDim.x * SA.warps);
+                thr *= fmaxf(busy, CUBICS_REG_THR_FLOOR);
+            }
             w = mean_nodes * node_ns >= thr;
         }
         worth_bins = __ballot_sync(FULLMASK, w);
@@ -640,7 +661,8 @@ struct Worker {
         if (may_donate) {
             // records owed to waiting workers, a bounded number per node
             const int owed = max((int)(p_head - p_prom), 0);
-            const int want = __shfl_sync(FULLMASK, min(owed, CUBICS_DONATE_MAX), 0);
+            owed_seen = __shfl_sync(FULLMASK, owed, 0);
+            const int want = min(owed_seen, CUBICS_DONATE_MAX);
             hungry = want > 0;
             if (want > 0) donate(want);
         }
@@ -717,7 +739,8 @@ struct Worker {
         if (lane == 0 && top > ws().maxd) ws().maxd = top;
         if (may_donate) {
             const int owed = max((int)(p_head - p_prom), 0);
-            const int want = __shfl_sync(FULLMASK, min(owed, CUBICS_DONATE_MAX), 0);
+            owed_seen = __shfl_sync(FULLMASK, owed, 0);
+            const int want = min(owed_seen, CUBICS_DONATE_MAX);
             hungry = want > 0;
             if (want > 0) donate(want);
         }
@@ -854,16 +877,17 @@ struct Worker {
             if (lane == 0) ws().wait_ns += global_ns() - t0;
             if (!got) return;
             taken = tick;
-            // the record counts in its bin now; its nodes are credited as they are explored
-            // (every 64th node and at the end), so that a large subtree still running
-            // already raises its bin's average
+            // the record's size bin (its share of unfixed variables); with running credit,
+            // it counts in its bin now and its nodes are credited as they are explored (every
+            // 64th node and at the end); otherwise it counts once it has finished
             pbin = ubin(count_unfixed(slots, nullptr));
             credited = tick;
             const long long t_taken = global_ns();
-            if (lane == 0) atomicAdd(&T->ucnt[pbin], 1u);
+            if (lane == 0 && !CUBICS_FINISHED_STATS) atomicAdd(&T->ucnt[pbin], 1u);
             explore();
             __syncwarp();
             if (lane == 0) {
+                if (CUBICS_FINISHED_STATS) atomicAdd(&T->ucnt[pbin], 1u);
                 atomicAdd(&T->usum[pbin], (unsigned long long)(tick - credited));
                 atomicAdd(&T->xnodes, (unsigned long long)(tick - taken));
                 atomicAdd(&T->xns, (unsigned long long)(global_ns() - t_taken));
@@ -934,6 +958,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
     wk.tick = 0;
     wk.hungry = 1;                   // the first nodes feed the idle workers at once
     wk.worth_bins = 0xffffffffu;     // nothing observed yet: every size is worth passing on
+    wk.owed_seen = 0;
     wk.taken = 0;
     wk.pbin = 0;
     wk.credited = 0;
@@ -1020,6 +1045,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
                 T->inst = i;
                 T->found = 0;
                 T->progress = 0;
+                SA.results[i].t_start = global_ns();
                 __threadfence();
                 atomicExch(&T->work, 1);
             }
@@ -1046,6 +1072,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
             r.status = fnd == 1 ? 1 : fnd == 2 ? CSP_ELIMIT_ : sols > 0 ? 1 : (st != 0 ? st : 0);
             r.n = (int)ib[H_N];
             r.sol_offset = SA.sol_off ? SA.sol_off[i] : 0;
+            r.t_end = global_ns();
         }
         __syncthreads();
     }

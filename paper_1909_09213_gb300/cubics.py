@@ -49,7 +49,8 @@ class csp_stats_t(C.Structure):
 
 class csp_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n", C.c_int32), ("nodes", C.c_uint64),
-                ("fails", C.c_uint64), ("solutions", C.c_uint64), ("sol_offset", C.c_int64)]
+                ("fails", C.c_uint64), ("solutions", C.c_uint64), ("sol_offset", C.c_int64),
+                ("ms", C.c_double)]
 
 
 # name -> (restype, argtypes): every entry point of include/cubics.h
