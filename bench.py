@@ -44,7 +44,8 @@ sys.path.insert(0, ROOT)
 METRIC = "search nodes propagated/sec and time-to-all/first-solution vs plain GPU first-fail"
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1909_09213_gb300", "csrc", f)
-                  for f in ("search.cuh", "device.cuh", "internal.h", "kernels_w1.cu")]
+                  for f in ("search.cuh", "device.cuh", "internal.h", "kernels_w1.cu",
+                            "kernels_w1r.cu")]
 
 
 def note(msg):

@@ -149,7 +149,8 @@ static __device__ bool q_take(uint32_t *seq, uint32_t *rec, uint32_t t, int dst,
 #endif
 
 // while workers wait for records, a busy worker checks the donation signal every this many
-// nodes (every 8th node otherwise)
+// nodes (every 8th node otherwise); a block's own queue (batch mode) every node: only the
+// grid-wide queue's counters are contended enough to make frequent checks cost
 #ifndef CUBICS_HUNGRY_EVERY
 #define CUBICS_HUNGRY_EVERY 4u
 #endif
@@ -592,7 +593,7 @@ struct Worker {
         uint32_t p_head = 0, p_prom = 0;
         // every 8th node; every node while workers are starved (ramp-up and the tail); never
         // in the first nodes of a record, so that small subtrees are not passed on
-        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? CUBICS_HUNGRY_EVERY - 1u : 7u)) == 0u) &&
+        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? (SA.batch ? 0u : CUBICS_HUNGRY_EVERY - 1u) : 7u)) == 0u) &&
                                 tick - taken >= CUBICS_DONATE_AFTER;
         if (may_donate && lane == 0) {
             p_head = ld_volatile(&T->head);
@@ -679,7 +680,7 @@ struct Worker {
         const bool polled = full || (tick & (CUBICS_POLL_EVERY - 1u)) == 0u;
         const int p_stop = polled ? poll() : 0;
         uint32_t p_head = 0, p_prom = 0;
-        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? CUBICS_HUNGRY_EVERY - 1u : 7u)) == 0u) &&
+        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? (SA.batch ? 0u : CUBICS_HUNGRY_EVERY - 1u) : 7u)) == 0u) &&
                                 tick - taken >= CUBICS_DONATE_AFTER;
         if (may_donate && lane == 0) {
             p_head = ld_volatile(&T->head);
