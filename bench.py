@@ -12,6 +12,8 @@ fixpoint and backtracked on the GPU).  Workloads:
 * linad256: 256 mixed linear/alldifferent instances (200 vars on 0..255), first solution;
 * rb_learned: 1024 held-out model-RB instances (n = 80, d = 20) with the learned brancher,
   trained first on subtree logs of 20 000 exhaustive searches, against first-fail;
+* linad_learned: the mixed batch with the learned brancher, trained first on the levels that
+  first-solution searches of 2048 training-seed instances refute, against first-fail;
 * lns: one round of parallel large neighbourhood search on a mixed instance.
 
 With the default workload the batch workloads also run once, after the timed steps, and are
@@ -611,6 +613,84 @@ class LinAdBatch(RBBatch):
         return self._oracle_instances(0, 1.5)
 
 
+class LearnedLinAd(LinAdBatch):
+    """The mixed linear/alldifferent batch with learned ordering: the network is trained on
+    the refuted levels of first-solution searches of 2048 training-seed instances (40 000
+    nodes at most each); a step solves the 256 graded instances in one launch with the
+    learned brancher.  The same batch under first-fail is timed alongside."""
+
+    # measured: 2048 x 40 000 nodes, 16 epochs gives the best network within ~30 s of
+    # collection and training (4096 x 10 000 and 3072 x 20 000 are slower at evaluation)
+    TRAIN, TRAIN_NODES, EPOCHS = 2048, 40_000, 16
+
+    def __init__(self, count=256):
+        super().__init__(count)
+        self.desc = (f"{count} mixed instances (200 vars on 0..255, 60 int_lin_le rows, 20 "
+                     f"alldifferent groups of 10), first solution, learned brancher trained on "
+                     f"first-solution searches of {self.TRAIN} training-seed instances, "
+                     f"{self.NODE_LIMIT} nodes at most per instance")
+        self.profile = "search_kernel_linad_learned.md"
+        self.kernel = "search_kernel_ext<8, false>"
+
+    def setup(self, K, stream):
+        from paper_1909_09213_gb300 import learn
+        t0 = time.time()
+        self.params, self.tinfo = learn.linad_training(self.TRAIN, self.TRAIN_NODES, self.EPOCHS)
+        self.prep_s = time.time() - t0
+        self.tiling = K.tiling(warps_per_block=4, smem_levels=4)
+        self.tune_entry = {"calib": None}
+        self.lim = K.limits(node_limit=self.NODE_LIMIT)
+        self.probs = [K.Csp(m) for m in self.models]
+        self.b = K.Batch(self.probs)
+        self.b.stream = stream
+        self.b.set_tiling(self.tiling)
+        w = np.ascontiguousarray(self.params, dtype=np.uint16)
+        K._check(K.lib().csp_batch_set_brancher(self.b.b, K.CSP_BR_LEARNED, w.ctypes.data_as(K._U16P)),
+                 "csp_batch_set_brancher")
+        self.b.bind(K.CSP_FIRST, stream)
+        self.rc, self.res = self.b.solve(K.CSP_FIRST, lim=self.lim, use_graph=True, bind=False)
+
+    def parity(self, st):
+        # every solution satisfies the model (oracle check); where both orderings decide an
+        # instance, they agree on SAT / UNSAT
+        from oracle import oracle as O
+        ok = True
+        for m, r, f in zip(self.models, self.res, self.ff_res):
+            if r["status"] == 1:
+                ok &= O.check_solution(O.OracleModel(m), self.sol[r["sol_offset"]:r["sol_offset"] + r["n"]])
+            if r["status"] >= 0 and f["status"] >= 0:
+                ok &= r["status"] == f["status"]
+        return ok
+
+    def extra(self, K, st):
+        b = K.Batch([K.Csp(m) for m in self.models])
+        b.stream = self.b.stream
+        b.set_tiling(self.tiling)
+        b.bind(K.CSP_FIRST, self.b.stream)
+        best = None
+        for _ in range(3):
+            rc, res = b.solve(K.CSP_FIRST, lim=self.lim, use_graph=True, bind=False)
+            ms = b.stats()["ms"]
+            if best is None or ms < best[0]:
+                best = (ms, res)
+        ff_ms, self.ff_res = best
+        out = super().extra(K, st)
+        out.update({"first_fail_gpu_ms": ff_ms,
+                    "first_fail_gpu_nodes": sum(r["nodes"] for r in self.ff_res),
+                    "first_fail_undecided": sum(r["status"] < 0 for r in self.ff_res),
+                    "first_fail_time_to_solution_ms": _time_to_solution(self.ff_res).get("time_to_solution_ms"),
+                    "learned_nodes": st["nodes"], "speedup_vs_first_fail": ff_ms / st["ms"],
+                    "training": {"instances": self.tinfo["train_instances"],
+                                 "node_limit": self.tinfo["node_limit"],
+                                 "logged_subtrees": self.tinfo["collect"]["entries"],
+                                 "train_nodes": self.tinfo["collect"]["nodes"],
+                                 "adam_steps": self.tinfo["train"]["steps"],
+                                 "mse": self.tinfo["train"]["mse_per_epoch"][-1],
+                                 "target_variance": self.tinfo["train"]["target_variance"],
+                                 "collect_and_train_s": self.prep_s}})
+        return out
+
+
 class LNSRound(RBBatch):
     """Parallel large neighbourhood search on a mixed instance (200 vars on 0..255, 60 rows,
     20 alldifferent groups) with objective min sum w_i x_i, w_i ~ U[1, 9]: one step is one
@@ -771,6 +851,8 @@ def make_workload(name):
         return LinAdBatch(256)
     if name == "rb_learned":
         return LearnedRB()
+    if name == "linad_learned":
+        return LearnedLinAd()
     if name == "lns":
         return LNSRound()
     raise SystemExit(f"unknown workload {name}")
@@ -899,7 +981,7 @@ def run_ours(args, rank, world, local_rank):
     if args.secondary and world == 1 and args.workload == "queens16":
         secondary = {}
         for name, make in (("rb4096", lambda: RBBatch(4096)), ("linad256", lambda: LinAdBatch(256)),
-                           ("rb_learned", lambda: LearnedRB())):
+                           ("rb_learned", lambda: LearnedRB()), ("linad_learned", lambda: LearnedLinAd())):
             note(f"secondary workload {name}")
             t0 = time.time()
             secondary[name] = make().secondary(K, stream)
@@ -928,7 +1010,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="queens16",
                     choices=["queens16", "queens15", "queens14", "rb4096", "rb_learned", "linad256",
-                             "lns"])
+                             "linad_learned", "lns"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--secondary", dest="secondary", action="store_true", default=True,
                     help="with the default workload: also run the batch workloads once "

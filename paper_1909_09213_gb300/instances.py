@@ -31,6 +31,7 @@ BASE_SEED = 20190920
 # config identifiers used to derive per-instance seeds
 CFG_QUEENS, CFG_RB, CFG_RB_TRAIN, CFG_RB_EVAL, CFG_LINAD, CFG_TINY = 1, 3, 40, 41, 5, 99
 CFG_LNS_OBJ, CFG_LNS_RELAX = 60, 61     # objective weights; neighbourhood draws
+CFG_LINAD_TRAIN = 42                    # training instances of the mixed workload's brancher
 
 
 def _mix64(z: int) -> int:

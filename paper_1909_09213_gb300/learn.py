@@ -21,8 +21,11 @@ from . import cubics as K
 N_FEAT = 16
 
 
-def collect(models, cap=4_000_000, sample=8, mode=K.CSP_ALL, stream=None):
-    """Subtree logs of exhaustive searches: a (rows, 17) float32 CUDA tensor."""
+def collect(models, cap=4_000_000, sample=8, mode=K.CSP_ALL, stream=None, lim=None):
+    """Subtree logs of the searches of `models` (exhaustive in CSP_ALL mode; in CSP_FIRST
+    mode the levels refuted before the first solution): a (rows, 17) float32 CUDA tensor.
+    `lim`: csp_limits (a node limit per instance; instances that reach it still log the
+    levels they completed)."""
     import torch
     probs = [K.Csp(m) for m in models]
     b = K.Batch(probs)
@@ -31,7 +34,7 @@ def collect(models, cap=4_000_000, sample=8, mode=K.CSP_ALL, stream=None):
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     K._check(K.lib().csp_batch_set_log(b.b, K._dp(log), K._dp(count), cap, sample), "csp_batch_set_log")
     t0 = time.time()
-    rc, res = b.solve(mode)
+    rc, res = b.solve(mode, lim=lim)
     if rc != 0:
         raise RuntimeError(f"logging search failed: {rc}")
     n = min(int(count.item()), cap)
@@ -110,6 +113,23 @@ def learning_config(train_count=20000, eval_count=1024, epochs=8, sample=1, cap=
             "first_fail_nodes": ev["first_fail"]["nodes"], "learned_nodes": ev["learned"]["nodes"],
             "sat": sum(s == 1 for s in ev["learned"]["status"]), "eval": ev, "params": params,
             "eval_models": eval_models}
+
+
+def linad_training(train_count=2048, node_limit=40_000, epochs=16):
+    """The brancher of the mixed linear/alldifferent workload: first-solution searches of
+    `train_count` training-seed instances of the same generator (200 vars on 0..255, 8-word
+    domains), at most `node_limit` nodes each, log the sizes of the levels they refute before
+    a solution (every completed level is a subtree without solution); the network is trained
+    on those logs.  Returns (bf16 params, info)."""
+    from . import instances as I
+    t0 = time.time()
+    models = I.linad_batch(train_count, config_id=I.CFG_LINAD_TRAIN)
+    gen_s = time.time() - t0
+    data, cinfo = collect(models, cap=8_000_000, sample=1, mode=K.CSP_FIRST,
+                          lim=K.limits(node_limit=node_limit))
+    params, tinfo = train(data, epochs=epochs)
+    return params, {"generate_s": gen_s, "collect": cinfo, "train": tinfo,
+                    "train_instances": train_count, "node_limit": node_limit}
 
 
 def evaluate(models, params_bf16, mode=K.CSP_FIRST, tiling=None, reps=1, stream=None):

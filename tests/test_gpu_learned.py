@@ -148,3 +148,34 @@ def test_learned_order_at_wider_domains(W):
         if r.solutions <= 100000:              # otherwise each stores an arbitrary 100000
             assert sorted(map(tuple, le_sols.tolist())) == sorted(map(tuple, ff_sols.tolist()))
             assert sorted(map(tuple, le_sols.tolist())) == sorted(map(tuple, r.sols.tolist()))
+
+
+def test_learned_first_solution_on_mixed_wide_instances():
+    """First-solution batches of small mixed linear/alldifferent instances over 0..255 (W = 8)
+    with the learned brancher: where both orderings decide an instance they agree on SAT /
+    UNSAT, every solution satisfies the model, and the oracle's verdict is met."""
+    models = [I.lin_alldiff(I.seed_for(I.CFG_LINAD_TRAIN, 900 + k), n=16, dmax=255, rows=8,
+                            kmin=3, kmax=6, groups=2, gsize=8, theta=0.3) for k in range(24)]
+    lim = K.limits(node_limit=100_000)
+    out = {}
+    for kind in (K.CSP_BR_FIRST_FAIL, K.CSP_BR_LEARNED):
+        b = K.Batch([K.Csp(m) for m in models])
+        if kind == K.CSP_BR_LEARNED:
+            w = np.ascontiguousarray(_weights(4), dtype=np.uint16)
+            K._check(K.lib().csp_batch_set_brancher(b.b, kind, w.ctypes.data_as(K._U16P)), "brancher")
+        rc, out[kind] = b.solve(K.CSP_FIRST, lim=lim)
+        assert rc == 0
+    decided = 0
+    for m, f, l in zip(models, out[K.CSP_BR_FIRST_FAIL], out[K.CSP_BR_LEARNED]):
+        assert K.Csp(m).layout()[1] == 8
+        om = O.OracleModel(m)
+        r = O.solve(om, mode=1, cap=1, node_limit=100_000)
+        for res in (f, l):
+            if res["status"] == 1:
+                assert O.check_solution(om, res["solution"]), m.name
+            if res["status"] >= 0 and r.status >= 0:
+                assert res["status"] == r.status, m.name
+        if f["status"] >= 0 and l["status"] >= 0:
+            decided += 1
+            assert f["status"] == l["status"], m.name
+    assert decided >= 12
