@@ -133,6 +133,14 @@ int csp_post_int_lin_le(csp_t *h, int32_t k, const int32_t *coef, const int32_t 
  * in the union of their domains.  vars: host array of k entries; repeats are CSP_EINVAL. */
 int csp_post_alldiff(csp_t *h, int32_t k, const int32_t *vars);
 
+/* all different over k <= 32 distinct variables, bounds-consistent (Section 4, second
+ * direction: a costlier propagation that prunes more): a bound of a member's domain stays only
+ * when the other members can take distinct values within their own [min, max] while the
+ * member takes that bound; holes are kept, so a bound that goes moves to the next value of
+ * the domain.  Complements csp_post_alldiff (value elimination); post both for both.
+ * vars: host array of k entries; repeats are CSP_EINVAL, k > 32 is CSP_ETOOBIG. */
+int csp_post_alldiff_bc(csp_t *h, int32_t k, const int32_t *vars);
+
 /* Binary relation as a tuple set (c2 of Section 1.1), arc-consistent.  allowed: host array
  * of (hi_x - lo_x + 1) rows of row_words uint32 words; bit b of row a allows the pair
  * (lo_x + a, lo_y + b).  row_words >= ceil((hi_y - lo_y + 1) / 32).  x == y is CSP_EINVAL. */

@@ -156,6 +156,7 @@ struct csp {
     std::vector<int32_t> ne_x, ne_y, ne_c;
     std::vector<LinRow> lin;
     std::vector<std::vector<int32_t>> ad;
+    std::vector<std::vector<int32_t>> adb;           // bounds-consistent alldifferent groups
     std::vector<Table> tab;
     int32_t lo0 = 0, W = 1;
     csp_tiling tiling{0, 0, 0, 0};
@@ -260,6 +261,23 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
             for (int32_t v : h->ad[g]) m[(size_t)v * amw + g / 32] |= 1u << (g % 32);
         for (uint32_t w : m) put(w);
     }
+    // bounds-consistent alldifferent groups (same layout as the alldiff ones)
+    const int nb = (int)h->adb.size();
+    B[H_N_ADB] = nb;
+    B[H_OFF_ADB_ROW] = (uint32_t)B.size();
+    uint32_t b0 = 0;
+    for (const auto &g : h->adb) { put(b0); put((uint32_t)g.size()); b0 += (uint32_t)g.size(); }
+    B[H_OFF_ADB_MEM] = (uint32_t)B.size();
+    for (const auto &g : h->adb) for (int32_t v : g) put((uint32_t)v);
+    const int bmw = (nb + 31) / 32;
+    B[H_ADB_MW] = bmw;
+    B[H_OFF_ADB_MASK] = (uint32_t)B.size();
+    {
+        std::vector<uint32_t> m((size_t)n * bmw, 0u);
+        for (int g = 0; g < nb; ++g)
+            for (int32_t v : h->adb[g]) m[(size_t)v * bmw + g / 32] |= 1u << (g % 32);
+        for (uint32_t w : m) put(w);
+    }
     // tables: 4-word entries, then the R/C matrices (32*W rows of W words each)
     const int nt = (int)h->tab.size();
     B[H_N_TAB] = nt;
@@ -310,6 +328,11 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
             for (size_t a = 0; a < r.var.size(); ++a)
                 for (size_t b = a + 1; b < r.var.size(); ++b) link(r.var[a], r.var[b]);
         }
+        for (const auto &g : h->adb) {     // counted with the alldifferent groups
+            for (int32_t v : g) { deg[v]++; kad[v]++; }
+            for (size_t a = 0; a < g.size(); ++a)
+                for (size_t b = a + 1; b < g.size(); ++b) link(g[a], g[b]);
+        }
         for (const auto &g : h->ad) {
             for (int32_t v : g) { deg[v]++; kad[v]++; }
             for (size_t a = 0; a < g.size(); ++a)
@@ -349,7 +372,7 @@ void encode(const csp *h, int W, std::vector<uint32_t> &B) {
                     put((uint32_t)(k * 64 + (size_t)__builtin_ctzll(w)));
     }
     // int_ne offset masks for a search that keeps one-word domains in registers
-    const bool ne_only = h->lin.empty() && h->ad.empty() && h->tab.empty();
+    const bool ne_only = h->lin.empty() && h->ad.empty() && h->tab.empty() && h->adb.empty();
     if (ne_only && W == 1 && n <= 32) {
         flags |= FLAG_NE_REG;
         while (B.size() & 1) B.push_back(0u);                 // 8-byte aligned pairs
@@ -582,6 +605,19 @@ int csp_post_alldiff(csp_t *h, int32_t k, const int32_t *vars) {
     return CSP_OK;
 }
 
+int csp_post_alldiff_bc(csp_t *h, int32_t k, const int32_t *vars) {
+    if (!h || k < 0 || (k > 0 && !vars)) return CSP_EINVAL;
+    if (k > ADB_MAX) return CSP_ETOOBIG;
+    std::vector<int32_t> g(vars, vars + k);
+    for (int32_t v : g) if (!var_ok(h, v)) return CSP_EINVAL;
+    std::vector<int32_t> s = g;
+    std::sort(s.begin(), s.end());
+    if (std::adjacent_find(s.begin(), s.end()) != s.end()) return CSP_EINVAL;
+    h->adb.push_back(g);
+    invalidate(h);
+    return CSP_OK;
+}
+
 int csp_post_table(csp_t *h, int32_t x, int32_t y, const uint32_t *allowed, int32_t row_words) {
     if (!var_ok(h, x) || !var_ok(h, y) || x == y || !allowed) return CSP_EINVAL;
     const int sx = h->hi[x] - h->lo[x] + 1, sy = h->hi[y] - h->lo[y] + 1;
@@ -624,6 +660,7 @@ int csp_clone(const csp_t *src, csp_t **out) {
     h->ne_c = src->ne_c;
     h->lin = src->lin;
     h->ad = src->ad;
+    h->adb = src->adb;
     h->tab = src->tab;
     h->lo0 = src->lo0;
     h->W = src->W;

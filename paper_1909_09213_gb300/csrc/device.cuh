@@ -295,6 +295,65 @@ __device__ bool revise_alldiff(const IV<ST> &I, int dom, int chg, int g) {
     return __any_sync(FULLMASK, fail);
 }
 
+// all different, bounds-consistent (Section 4, second direction), by Hall intervals on the
+// interval relaxation: when the members whose [min, max] lie inside an interval [a, b] are as
+// many as its values, they use all of them, so no other member may keep a bound inside it
+// (its min moves above b, its max below a; holes are kept, so a bound moves to the next value
+// of the domain); more members than values fails.  Every Hall interval equals the interval
+// from the least min to the greatest max of its members, so the candidates are the pairs
+// (a member's min, a member's max).  Lane j holds member j (k <= ADB_MAX = 32); passes over
+// the candidates repeat until one changes nothing.  Returns true on failure.
+template <int W, bool ST>
+__device__ bool revise_alldiff_bc(const IV<ST> &I, int dom, int chg, int g) {
+    const int lane = lane_id();
+    const int grp = (int)I.w(H_OFF_ADB_ROW) + 2 * g;
+    const int m0 = (int)I.w(grp), k = (int)I.w(grp + 1);
+    const bool act = lane < k;
+    const int v = act ? (int)I.w((int)I.w(H_OFF_ADB_MEM) + m0 + lane) : 0;
+    const int dv = dom + v * W;
+    int lo = act ? dom_min<W>(dv) : 0, hi = act ? dom_max<W>(dv) : 0;
+    if (__any_sync(FULLMASK, act && lo < 0)) return true;
+    bool mine_changed = false;
+    for (bool again = true; again;) {
+        again = false;
+        for (int t = 0; t < k; ++t) {
+            for (int u = 0; u < k; ++u) {
+                const int a = __shfl_sync(FULLMASK, lo, t), b = __shfl_sync(FULLMASK, hi, u);
+                if (b < a) continue;
+                const uint32_t inside = __ballot_sync(FULLMASK, act && lo >= a && hi <= b);
+                const int cnt = __popc(inside);
+                if (cnt > b - a + 1) return true;
+                if (cnt < b - a + 1) continue;
+                bool moved = false;
+                if (act && !((inside >> lane) & 1u) && ((lo >= a && lo <= b) || (hi >= a && hi <= b))) {
+                    const bool cut_lo = lo >= a && lo <= b, cut_hi = hi >= a && hi <= b;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        uint32_t keep = FULLMASK;
+                        if (cut_lo) keep &= keep_ge(w, b + 1);
+                        if (cut_hi) keep &= keep_le(w, a - 1);
+                        if (SM[dv + w] & ~keep) atomicAnd(&SM[dv + w], keep);
+                    }
+                    lo = dom_min<W>(dv);
+                    hi = dom_max<W>(dv);
+                    moved = true;
+                    mine_changed = true;
+                }
+                if (__any_sync(FULLMASK, moved)) {
+                    again = true;
+                    if (__any_sync(FULLMASK, act && lo < 0)) {
+                        if (mine_changed) mark_changed(chg, v);
+                        return true;
+                    }
+                }
+            }
+        }
+    }
+    if (mine_changed) mark_changed(chg, v);
+    __syncwarp();
+    return false;
+}
+
 // Constraints of a kind whose scope meets the event set, from per-variable masks
 // (mw words per variable at `mask`; bit c of word k = constraint 32k + c).  Calls f(c).
 template <bool ST, typename F>
@@ -500,7 +559,7 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
     const int adj_start = (int)I.w(H_OFF_ADJ_START);
     const int adj = (int)I.w(H_OFF_ADJ);
     const int n_tab = (int)I.w(H_N_TAB);
-    const int n_lin = (int)I.w(H_N_LIN), n_ad = (int)I.w(H_N_AD);
+    const int n_lin = (int)I.w(H_N_LIN), n_ad = (int)I.w(H_N_AD), n_adb = (int)I.w(H_N_ADB);
     const bool has_ne = I.w(H_N_NE) != 0u;
     for (;;) {
         // 1. this round's events: the variables changed in the previous round
@@ -705,7 +764,7 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
             }
             if (__any_sync(FULLMASK, fail)) return true;
         }
-        // 5. linear rows and 6. alldifferent groups whose scope changed
+        // 5. linear rows and 6. alldifferent groups whose scope changed (value elimination)
         if (n_lin) {
             if (for_scheduled<ST>(I, evs, (int)I.w(H_OFF_LIN_MASK), (int)I.w(H_LIN_MW), [&](int r) {
                     if (lane == 0) evals++;
@@ -717,6 +776,14 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
             if (for_scheduled<ST>(I, evs, (int)I.w(H_OFF_AD_MASK), (int)I.w(H_AD_MW), [&](int g) {
                     if (lane == 0) evals++;
                     return revise_alldiff<W, ST>(I, dom, chg, g);
+                }))
+                return true;
+        }
+        // 7. bounds-consistent alldifferent groups whose scope changed
+        if (n_adb) {
+            if (for_scheduled<ST>(I, evs, (int)I.w(H_OFF_ADB_MASK), (int)I.w(H_ADB_MW), [&](int g) {
+                    if (lane == 0) evals++;
+                    return revise_alldiff_bc<W, ST>(I, dom, chg, g);
                 }))
                 return true;
         }

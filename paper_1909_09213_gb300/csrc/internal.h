@@ -13,7 +13,8 @@ namespace cubics {
 
 constexpr int MAX_VARS = 1024;          // NW = ceil(n/32) <= 32 event words per worker
 constexpr int MAX_W = 8;                // 256-value window
-constexpr int HDR_WORDS = 32;
+constexpr int HDR_WORDS = 48;
+constexpr int ADB_MAX = 32;             // members of a bounds-consistent alldifferent group
 constexpr uint32_t FLAG_TRIVIAL_FAIL = 1u;  // a row with no terms and rhs < 0
 constexpr uint32_t FLAG_NE_ONLY = 2u;       // int_ne constraints only (no lin, alldiff, table)
 constexpr uint32_t FLAG_NE_REG = 4u;        // also one word per domain and n <= 32: the search
@@ -37,6 +38,8 @@ enum Hdr {
     H_OFF_NB_START, H_OFF_NB,         // neighbour lists: n+1 starts; neighbour indices
     H_MAXDEG,                         // largest constraint degree of a variable
     H_OFF_NEMASK,                     // FLAG_NE_REG: n x 32 offset masks of 2 words (below)
+    H_N_ADB, H_OFF_ADB_ROW, H_OFF_ADB_MEM, H_ADB_MW, H_OFF_ADB_MASK,   // bounds-consistent
+                                      // alldifferent groups, laid out as the alldiff ones
     H_COUNT
 };
 
@@ -53,7 +56,7 @@ static_assert(H_COUNT <= HDR_WORDS, "header too long");
 // offsets never meet a one-word domain).  Indexed fixed variable first, so that the 32 lanes
 // of a warp read the masks of one fixed variable from consecutive words.
 // lin row: 3 words (first term, number of terms, rhs); term: 2 words (coef, var)
-// alldiff group: 2 words (first member, number of members)
+// alldiff group (both kinds): 2 words (first member, number of members)
 // table: 4 words (x, y, word offset of R, word offset of C); R and C hold 32*W rows of W
 //        words: R row a = values of y compatible with x = lo0 + a, C row b the transpose.
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "csp_post_int_ne": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
     "csp_post_int_lin_le": (C.c_int, [_VP, C.c_int32, _I32P, _I32P, C.c_int32]),
     "csp_post_alldiff": (C.c_int, [_VP, C.c_int32, _I32P]),
+    "csp_post_alldiff_bc": (C.c_int, [_VP, C.c_int32, _I32P]),
     "csp_post_table": (C.c_int, [_VP, C.c_int32, C.c_int32, _U32P, C.c_int32]),
     "csp_layout": (C.c_int, [_VP, _I32P, _I32P, _I32P]),
     "csp_root_domains": (C.c_int, [_VP, _U32P]),
@@ -172,8 +173,6 @@ class Csp:
     """One CSP (X, D, C) built through csp_create / csp_post_* from a CspModel."""
 
     def __init__(self, model):
-        if getattr(model, "alldiff_bc", None):
-            raise ValueError("bounds-consistent alldifferent has no device propagator yet")
         L = lib()
         self.model = model
         h = _VP()
@@ -193,6 +192,9 @@ class Csp:
         for g in model.alldiff:
             v = _i32(g)
             _check(L.csp_post_alldiff(h, len(v), _ptr(v, _I32P)), "csp_post_alldiff")
+        for g in getattr(model, "alldiff_bc", []):
+            v = _i32(g)
+            _check(L.csp_post_alldiff_bc(h, len(v), _ptr(v, _I32P)), "csp_post_alldiff_bc")
         for (x, y, allowed) in model.tables:
             al = np.asarray(allowed, dtype=bool)
             rw = (al.shape[1] + 31) // 32

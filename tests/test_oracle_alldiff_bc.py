@@ -1,8 +1,8 @@
 """Oracle: bounds-consistent alldifferent (the stronger propagation Section 4 proposes as its
 second direction).  The C oracle decides supports by bipartite matching; here the same
 closure is recomputed by enumerating the interval relaxation, and checked against closed
-forms, brute-force solutions and evaluation order.  There is no device propagator yet: the
-library refuses models that carry one."""
+forms, brute-force solutions and evaluation order.  The device propagator is checked against
+this oracle in tests/test_gpu_alldiff_bc.py."""
 import itertools
 
 import pytest
@@ -110,10 +110,24 @@ def test_search_keeps_the_solution_set(seed):
     assert (rb.solutions, rb.hash_sum, rb.hash_xor) == (rp.solutions, rp.hash_sum, rp.hash_xor)
 
 
-def test_library_refuses_models_it_cannot_propagate():
+def test_library_accepts_groups_and_validates_them():
+    """Host side of csp_post_alldiff_bc: groups are accepted (the device propagator exists);
+    repeated or bad variables are CSP_EINVAL, more than 32 members CSP_ETOOBIG."""
+    import ctypes as C
     from paper_1909_09213_gb300 import cubics as K
-    with pytest.raises(ValueError):
-        K.Csp(_model([0, 0], [1, 1]))
+    K.Csp(_model([0, 0], [1, 1]))
+    L = K.lib()
+    h = C.c_void_p()
+    lo = (C.c_int32 * 40)(*([0] * 40))
+    hi = (C.c_int32 * 40)(*([50] * 40))
+    assert L.csp_create(C.byref(h), 40, lo, hi) == 0
+    try:
+        assert L.csp_post_alldiff_bc(h, 2, (C.c_int32 * 2)(3, 3)) == K.CSP_EINVAL
+        assert L.csp_post_alldiff_bc(h, 2, (C.c_int32 * 2)(3, 40)) == K.CSP_EINVAL
+        assert L.csp_post_alldiff_bc(h, 33, (C.c_int32 * 33)(*range(33))) == K.CSP_ETOOBIG
+        assert L.csp_post_alldiff_bc(h, 32, (C.c_int32 * 32)(*range(32))) == 0
+    finally:
+        L.csp_destroy(h)
 
 
 def _hall_interval_closure(doms):
