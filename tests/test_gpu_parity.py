@@ -386,6 +386,30 @@ def test_partitioned_tree_sums_to_the_whole(nparts):
             assert got[k] == st_whole[k], (m.name, k)
 
 
+@pytest.mark.parametrize("depth,nparts", [(2, 2), (3, 3), (4, 8)])
+def test_tree_cut_at_depth_k_sums_to_the_whole(depth, nparts):
+    """shard.solve_part: the tree cut at depth k (levels expanded with csp_propagate, units
+    solved as batches of root copies); the parts, run one after another on this GPU, combine
+    to the undivided search.  In first-solution mode some part finds a valid solution."""
+    from paper_1909_09213_gb300 import shard
+    for m in [I.queens(12), I.model_rb(I.seed_for(I.CFG_RB, 11), 14, 7), mixed_model(210, 40, 5),
+              strided_queens(9, 31)]:
+        rc, whole, _ = K.Csp(m).solve(K.CSP_ALL, 0)
+        assert rc == 0
+        parts = [shard.solve_part(K.Csp(m), part, nparts, depth) for part in range(nparts)]
+        assert sum(pt["units"] for pt in parts) == parts[0]["units_total"]
+        got = shard.combine(parts)
+        for k in shard.FIELDS:
+            assert got[k] == whole[k], (m.name, k)
+        found = []
+        for part in range(nparts):
+            st, (f, sol) = shard.solve_part(K.Csp(m), part, nparts, depth, mode=K.CSP_FIRST, chunk=8)
+            if f:
+                assert O.check_solution(O.OracleModel(m), sol), m.name
+            found.append(f)
+        assert any(found) == (whole["solutions"] > 0), m.name
+
+
 # ----------------------------------------------------------------------------- limits, errors
 
 def test_node_limit():

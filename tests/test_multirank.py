@@ -114,3 +114,164 @@ def test_units_and_partition_cover_everything():
         assert got == list(range(37))
     with pytest.raises(ValueError):
         shard.partition(2, 2)
+
+
+# ----------------------------------------------------------------------------- depth-k split
+
+def _oracle_tools(m):
+    """The library's layout and root domains (host-only calls) and a propagate function with
+    the oracle's fixpoint standing in for the device's (same (count, n*W) bitset layout)."""
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import numpy as np
+    from _util import bits_to_flags, flags_to_bits
+    from oracle import oracle as O
+    from paper_1909_09213_gb300 import cubics as K
+    p = K.Csp(m)
+    n, W, lo0 = p.layout()
+    om = O.OracleModel(m)
+
+    def propagate(states):
+        out, failed = [], []
+        for s in states:
+            f, d = O.propagate(om, bits_to_flags(om, s, n, W, lo0), variant=1)
+            failed.append(f)
+            out.append(flags_to_bits(om, d, n, W, lo0) if not f else s)
+        return np.array(out, dtype=np.uint32), np.array(failed)
+
+    def solve_unit(u, mode=0):
+        return O.solve(om, mode=mode, cap=1, variant=1, dom=bits_to_flags(om, u, n, W, lo0))
+
+    return p, n, W, om, propagate, solve_unit
+
+
+def _share(m, depth, part, nparts):
+    from paper_1909_09213_gb300 import shard
+    p, n, W, om, propagate, solve_unit = _oracle_tools(m)
+    units, nodes, fails = shard.split_units(propagate, p.root_domains().ravel(), n, W, depth)
+    st = {"nodes": nodes if part == 0 else 0, "fails": fails if part == 0 else 0,
+          "solutions": 0, "sol_hash_sum": 0, "sol_hash_xor": 0}
+    for u in units[part::nparts]:
+        r = solve_unit(u)
+        st = shard.combine([st, {"nodes": r.nodes, "fails": r.fails, "solutions": r.solutions,
+                                 "sol_hash_sum": r.hash_sum, "sol_hash_xor": r.hash_xor}])
+    return st, len(units)
+
+
+def _tiny_mixed():
+    from paper_1909_09213_gb300 import instances as I
+    return I.random_tiny(I.seed_for(I.CFG_TINY, 70003))
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3, 5])
+def test_depth_k_split_sums_to_the_whole_search(depth):
+    """Every rank count and depth: the ranks' shares of a tree cut at depth k combine to the
+    undivided search (nodes, fails, solutions, both hashes)."""
+    from oracle import oracle as O
+    from paper_1909_09213_gb300 import instances as I
+    from paper_1909_09213_gb300 import shard
+    for m in (I.queens(8), I.worked_example("lin", "table"), _tiny_mixed()):
+        full = O.solve(O.OracleModel(m), variant=1)
+        want = {"nodes": full.nodes, "fails": full.fails, "solutions": full.solutions,
+                "sol_hash_sum": full.hash_sum, "sol_hash_xor": full.hash_xor}
+        for nparts in (1, 2, 3, 8):
+            parts = [_share(m, depth, r, nparts)[0] for r in range(nparts)]
+            assert shard.combine(parts) == want, (m.name, depth, nparts)
+    # 8-queens at depth 3: the units are the consistent placements of the first three queens
+    _, count = _share(I.queens(8), 3, 0, 1)
+    assert count > 100
+
+
+def _split_worker(rank, world, port, outdir, depth):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=30))
+    from paper_1909_09213_gb300 import instances as I
+    from paper_1909_09213_gb300 import shard
+    st, _ = _share(I.queens(9), depth, rank, world)
+    res = {"combined": shard.combine_across_ranks(st)}
+    with open(os.path.join(outdir, f"rank{rank}.json"), "w") as f:
+        json.dump(res, f)
+    dist.destroy_process_group()
+
+
+def test_three_ranks_share_a_tree_cut_at_depth_3():
+    from oracle import oracle as O
+    from paper_1909_09213_gb300 import instances as I
+    port = _free_port()
+    with tempfile.TemporaryDirectory() as d:
+        ctx = mp.get_context("spawn")
+        procs = [ctx.Process(target=_split_worker, args=(r, 3, port, d, 3)) for r in range(3)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=180)
+            assert not p.is_alive() and p.exitcode == 0
+        out = [json.load(open(os.path.join(d, f"rank{r}.json"))) for r in range(3)]
+    full = O.solve(O.OracleModel(I.queens(9)), variant=1)
+    for o in out:
+        assert o["combined"] == {"nodes": full.nodes, "fails": full.fails,
+                                 "solutions": full.solutions, "sol_hash_sum": full.hash_sum,
+                                 "sol_hash_xor": full.hash_xor}
+
+
+def _first_worker(rank, world, port, outdir, which):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=30))
+    from paper_1909_09213_gb300 import instances as I
+    from paper_1909_09213_gb300 import shard
+    m = I.queens(10) if which == "sat" else I.queens(3)
+    p, n, W, om, propagate, solve_unit = _oracle_tools(m)
+    units, _, _ = shard.split_units(propagate, p.root_domains().ravel(), n, W, 3)
+
+    def solve_chunk(piece):
+        nodes = 0
+        for u in piece:
+            r = solve_unit(u, mode=1)
+            nodes += r.nodes
+            st = {"nodes": nodes, "fails": 0, "solutions": 0, "sol_hash_sum": 0, "sol_hash_xor": 0}
+            if r.status == 1:
+                return True, [int(v) for v in r.sols[0]], st
+        return False, None, {"nodes": nodes, "fails": 0, "solutions": 0, "sol_hash_sum": 0,
+                             "sol_hash_xor": 0}
+
+    found, sol, st, ran = shard.first_over_ranks(units, rank, world, solve_chunk,
+                                                 shard.any_rank, chunk=4)
+    from oracle import oracle as O
+    res = {"found": found, "sol": sol, "ran": ran, "units": len(units),
+           "valid": bool(sol is None or O.check_solution(om, sol))}
+    with open(os.path.join(outdir, f"rank{rank}.json"), "w") as f:
+        json.dump(res, f)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("which", ["sat", "unsat"])
+def test_first_solution_stops_every_rank(which):
+    """FIRST mode over a shared tree: the ranks OR a found flag after each chunk of units,
+    so every rank stops after the same chunk once one has a solution (10-queens, SAT); when
+    there is none (3-queens, UNSAT) every unit is searched and no rank reports one."""
+    port = _free_port()
+    with tempfile.TemporaryDirectory() as d:
+        ctx = mp.get_context("spawn")
+        procs = [ctx.Process(target=_first_worker, args=(r, 2, port, d, which)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=180)
+            assert not p.is_alive() and p.exitcode == 0
+        out = [json.load(open(os.path.join(d, f"rank{r}.json"))) for r in range(2)]
+    assert all(o["valid"] for o in out)
+    if which == "sat":
+        assert all(o["found"] for o in out)
+        assert any(o["sol"] is not None for o in out)
+        # the first chunk already holds solutions: nobody searched its whole share
+        assert all(o["ran"] <= 1 for o in out) and out[0]["units"] > 8
+    else:
+        assert not any(o["found"] for o in out)
