@@ -142,6 +142,12 @@ def rb_tightness(alpha: float = 0.8, r: float = 0.7) -> float:
     return 1.0 - math.exp(-alpha / r)
 
 
+def rb_threshold_tightness(n: int, d: int, r: float = 0.7) -> float:
+    """The tightness at which the expected number of solutions of model RB is 1 (first-moment
+    threshold): n ln d + r n ln n ln(1 - p) = 0, so p* = 1 - exp(-ln d / (r ln n))."""
+    return 1.0 - math.exp(-math.log(d) / (r * math.log(n)))
+
+
 def model_rb(seed: int, n: int, d: int, alpha: float = 0.8, r: float = 0.7,
              p: float | None = None) -> CspModel:
     """One model-RB instance: m = round(r n ln n) binary tables, each over two distinct

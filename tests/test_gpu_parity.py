@@ -563,3 +563,30 @@ def test_batch_full_size_model_rb_verdicts_against_oracle_file():
         if r["status"] == 1:
             assert O.check_solution(O.OracleModel(m), r["solution"]), i
     assert decided >= 500
+
+
+def test_batch_transfer_byte_accounting():
+    """csp_stats of a batch: h2d_bytes counts the upload since the previous successful
+    collect (the encoded instances plus 16 bytes of offsets per instance), d2h_bytes the
+    launch counters, the per-instance records and, when asked for, the solutions."""
+    import ctypes as C
+    models = _rb_small(16, first=40)
+    b = K.Batch([K.Csp(m) for m in models])
+    rc, _ = b.solve(K.CSP_FIRST)                  # uploads, launches, collects with solutions
+    assert rc == 0
+    st = b.stats()
+    words = K.lib().csp_batch_solution_words(b.b)
+    assert st["h2d_bytes"] > 16 * len(models) and st["h2d_bytes"] % 4 == 0
+    res = (K.csp_result * len(models))()
+    sol = np.zeros(max(words, 1), np.int32)
+    K._check(K.lib().csp_batch_launch(b.b, None, 0), "launch")
+    assert K.lib().csp_batch_collect(b.b, res, None) == 0
+    st_none = b.stats()
+    assert st_none["h2d_bytes"] == 0                  # nothing uploaded since the last collect
+    K._check(K.lib().csp_batch_launch(b.b, None, 0), "launch")
+    assert K.lib().csp_batch_collect(b.b, res, sol.ctypes.data_as(K._I32P)) == 0
+    st_sol = b.stats()
+    assert st_sol["d2h_bytes"] - st_none["d2h_bytes"] == 4 * words
+    b.set_tiling(K.tiling(warps_per_block=2))          # forces a new upload
+    rc, _ = b.solve(K.CSP_FIRST)
+    assert rc == 0 and b.stats()["h2d_bytes"] == st["h2d_bytes"]

@@ -428,6 +428,17 @@ def test_model_rb_shape():
     assert len(m.tables) == 245 and int((~m.tables[0][2]).sum()) == 272
 
 
+def test_model_rb_threshold_tightness():
+    # at p*, ln E[#solutions] = n ln d + m ln(1 - p*) with m = r n ln n is exactly zero
+    for n, d in ((80, 20), (30, 16), (20, 8), (60, 32)):
+        p = I.rb_threshold_tightness(n, d)
+        assert abs(n * math.log(d) + 0.7 * n * math.log(n) * math.log(1 - p)) < 1e-9
+    assert abs(I.rb_threshold_tightness(80, 20) - 0.6234) < 1e-4
+    # the learning configuration's evaluation set at the configured p is far above it:
+    # ln E = 80 ln 20 + 245 ln(1 - 0.681093) = -40.3
+    assert abs(80 * math.log(20) + 245 * math.log(1 - I.rb_tightness()) + 40.3) < 0.1
+
+
 def test_generators_are_deterministic():
     a, b = I.rb_batch(3), I.rb_batch(3)
     for ma, mb in zip(a, b):
