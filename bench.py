@@ -18,7 +18,8 @@ fixpoint and backtracked on the GPU).  Workloads:
 
 With the default workload the batch workloads also run once, after the timed steps, and are
 reported under config.secondary: verdicts against the oracle, per-instance time to solution,
-batched against one-at-a-time first-fail search, learned against first-fail ordering.  The
+batched against one-at-a-time first-fail search, learned against first-fail ordering, and
+the propagation of large nodes with a warp or a whole block per node.  The
 CPU baseline is the oracle on one host core and, for N-queens, on every host core.
 
 Prints one JSON line.
@@ -204,6 +205,67 @@ def queens_oracle_all_cores(N, budget_s=15.0):
             "sample": (f"{N}-queens subtrees with x0, x1, x2 fixed, consistent prefixes in "
                        f"lexicographic order fed to {cores} processes: {k} finished "
                        f"({nodes} nodes, {dt:.1f} s wall)")}
+
+
+def huge_node_propagation(K, count=2048, reps=3):
+    """Constraint-parallel propagation of large nodes: fixpoints of `count` random sub-states
+    (each present value kept with probability 7/8) of two 1000-variable instances, one
+    csp_propagate call per shape: a warp per state, or a block of 128..1024 threads per state
+    sharing out the constraints.  Kernel time from the call's events (best of `reps`); every
+    shape must give the same fixpoints, and a sample of states is checked against the oracle."""
+    from oracle import oracle as O
+    from paper_1909_09213_gb300 import instances as I
+    from paper_1909_09213_gb300 import tune
+    out = {}
+    rng = np.random.default_rng(20190920)
+    cases = (("mixed: 1000 vars on 0..255 (8 words), 300 rows, 100 alldifferent groups of 10",
+              I.lin_alldiff(I.seed_for(I.CFG_LINAD, 77), n=1000, dmax=255, rows=300, groups=100,
+                            gsize=10)),
+             ("model RB: 1000 vars, d = 32 (1 word), 4835 tables",
+              I.model_rb(I.seed_for(I.CFG_RB, 999_001), 1000, 32)))
+    for desc, m in cases:
+        p = K.Csp(m)
+        n, W, lo0 = p.layout()
+        root = p.root_domains().ravel()
+        r = [rng.integers(0, 1 << 32, size=(count, n * W), dtype=np.uint64).astype(np.uint32)
+             for _ in range(3)]
+        states = root[None, :] & (r[0] | r[1] | r[2])
+        shapes, ref = {}, None
+        for tpn in (32, 128, 256, 512, 1024):
+            p.set_tiling(K.tiling(threads_per_node=tpn))
+            try:
+                best = None
+                for _ in range(reps):
+                    dout, failed = p.propagate(states)
+                    ms = p.stats()["ms"]
+                    best = ms if best is None else min(best, ms)
+            except K.CspError as e:
+                shapes[tpn] = {"error": str(e)}
+                continue
+            if ref is None:
+                ref = (dout, failed)
+            same = bool(np.array_equal(failed, ref[1]) and np.array_equal(dout[~failed], ref[0][~failed]))
+            shapes[tpn] = {"kernel_ms": best, "states_per_s": count / (best * 1e-3),
+                           "failed": int(failed.sum()), "same_fixpoints": same}
+        om = O.OracleModel(m)
+        ok = True
+        for k in range(4):
+            flags = np.zeros(int(om.off[-1]), dtype=np.uint8)
+            for i in range(n):
+                for j in range(int(om.size[i])):
+                    b = int(om.lo[i]) + j - lo0
+                    flags[om.off[i] + j] = (int(states[k, i * W + b // 32]) >> (b % 32)) & 1
+            of, od = O.propagate(om, flags, variant=1)
+            ok &= of == bool(ref[1][k])
+            if not of:
+                for i in range(n):
+                    for j in range(int(om.size[i])):
+                        b = int(om.lo[i]) + j - lo0
+                        ok &= bool((int(ref[0][k, i * W + b // 32]) >> (b % 32)) & 1) == bool(od[om.off[i] + j])
+        t, entry = tune.tune_propagate(m, states[:512], reps=1, use_cache=False)
+        out[desc] = {"states": count, "state_bytes": n * W * 4, "shapes": shapes,
+                     "oracle_sample_parity": bool(ok), "tuned_threads_per_node": t.threads_per_node}
+    return out
 
 
 class Queens:
@@ -1033,6 +1095,10 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.time()
             secondary[name] = make().secondary(K, stream)
             secondary[name]["wall_s"] = round(time.time() - t0, 1)
+        note("secondary: propagation of large nodes, warp or block per node")
+        t0 = time.time()
+        secondary["huge_node_propagation"] = huge_node_propagation(K)
+        secondary["huge_node_propagation"]["wall_s"] = round(time.time() - t0, 1)
     config = {"workload": wl.desc, "nodes_per_step": st["nodes"],
               "l2": "flushed before every step (256 MiB write, untimed)",
               "workers": st["workers"], "blocks": st["blocks"],

@@ -71,6 +71,12 @@ typedef struct {
                                  with CSP_EINVAL */
     int32_t smem_levels;      /* search-stack levels kept in shared memory per worker */
     int32_t queue_records;    /* capacity of each work queue (power of two) */
+    int32_t threads_per_node; /* 0 or 32: a warp per node (the search kernels' only shape);
+                                 64..1024 (a multiple of 32): csp_propagate gives each domain
+                                 state a whole block, its warps sharing out the constraints of
+                                 each kind (constraint-parallel propagation of one node too
+                                 large for a warp, Section 2.2's grouping by kind); a search
+                                 plan with it is CSP_EINVAL */
 } csp_tiling;
 
 typedef struct {
@@ -206,9 +212,12 @@ int csp_upload(csp_t *h, int32_t mode, int64_t cap);
 int csp_launch(csp_t *h, const csp_limits *lim);
 int csp_collect(csp_t *h, int32_t *sol_out);
 
-/* One fixpoint per domain state (test hook; Section 1.1, constraint propagation).
- * dom_in, dom_out: host arrays of count * n * W words (layout of csp_layout); failed: host
- * array of count int32 (1 = some domain became empty; dom_out is then unspecified). */
+/* One fixpoint per domain state (test hook, and the level expansion of a depth-k search-space
+ * partition; Section 1.1, constraint propagation).  dom_in, dom_out: host arrays of
+ * count * n * W words (layout of csp_layout); failed: host array of count int32 (1 = some
+ * domain became empty; dom_out is then unspecified).  A warp per state, or a block per state
+ * when csp_tiling.threads_per_node > 32.  csp_stats afterwards: nodes = count, fails = the
+ * failed states, ms = the kernel's device time. */
 int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom_out,
                   int32_t *failed);
 

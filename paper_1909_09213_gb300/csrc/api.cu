@@ -21,7 +21,7 @@ cudaError_t occupancy_search(int W, bool staged, int kind, int threads, size_t s
 cudaError_t launch_init_single(const SearchArgs &A, cudaStream_t st);
 cudaError_t launch_init_batch(const SearchArgs &A, int teams, cudaStream_t st);
 cudaError_t launch_propagate(int W, bool staged, const PropArgs &P, int blocks, int threads,
-                             size_t smem, cudaStream_t st);
+                             size_t smem, cudaStream_t st, bool block_per_node);
 cudaError_t probe_smem(void *out, cudaStream_t st, int sms, int reps, double *gbs);
 cudaError_t mlp_pack(const uint16_t *params, uint32_t *packed, cudaStream_t st);
 }  // namespace cubics
@@ -78,6 +78,8 @@ struct Shape {
 // logging is on).
 int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batch, bool learned,
                bool logging, int nmax, int ntab, bool reg, Shape *s) {
+    // the search kernels run one node per warp; a block per node is a propagate-only shape
+    if (t.threads_per_node > 32) return CSP_EINVAL;
     s->kind = (learned || logging) ? KERN_EXT : reg ? KERN_REG : KERN_PLAIN;
     // one-word tables are revised from a per-warp list of the scheduled ones
     s->list_words = (W == 1 && ntab > 0) ? (ntab + 31) & ~31 : 0;
@@ -696,13 +698,17 @@ int csp_layout(const csp_t *h, int32_t *n, int32_t *W, int32_t *lo0) {
     return CSP_OK;
 }
 
+// queue capacity a power of two; threads per node 0 or a multiple of 32 up to 1024
+static bool tiling_ok(const csp_tiling &t) {
+    const int tp = t.threads_per_node;
+    return !(t.queue_records & (t.queue_records - 1)) && tp >= 0 && tp <= 1024 && tp % 32 == 0;
+}
+
 int csp_set_tiling(csp_t *h, const csp_tiling *t) {
     if (!h) return CSP_EINVAL;
-    h->tiling = t ? *t : csp_tiling{0, 0, 0, 0};
-    if (h->tiling.queue_records & (h->tiling.queue_records - 1)) {
-        h->tiling = csp_tiling{0, 0, 0, 0};
-        return CSP_EINVAL;
-    }
+    const csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0, 0};
+    if (!tiling_ok(nt)) return CSP_EINVAL;
+    h->tiling = nt;
     invalidate(h);
     return CSP_OK;
 }
@@ -877,21 +883,45 @@ int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom
     P.failed = (int32_t *)(h->ws + L.o_sols);
     P.count = count;
     const int cons4 = ((int)B[H_CONS_WORDS] + 3) & ~3;
-    const int warps = 8;
-    const size_t per_warp = (size_t)(((h->n * h->W + 3) & ~3) + 64) * 4;
-    size_t smem = per_warp * warps;
+    const size_t per_state = (size_t)(((h->n * h->W + 3) & ~3) + 64) * 4;   // state, chg, evs
+    const int tpn = h->tiling.threads_per_node;
+    const bool block_per_node = tpn > 32;
+    // a warp per state: up to 8 states per block, as many as fit; a block per state: tpn threads
+    int warps = block_per_node ? tpn / 32 : 8;
+    if (!block_per_node)
+        while (warps > 1 && per_state * warps > SMEM_MAX) --warps;
+    size_t smem = per_state * (block_per_node ? 1 : warps);
     P.stage_words = (smem + (size_t)cons4 * 4 <= SMEM_MAX) ? cons4 : 0;
     smem += (size_t)P.stage_words * 4;
     if (smem > SMEM_MAX) return CSP_ETOOBIG;
-    const int blocks = std::max(1, std::min(4096, (count + warps - 1) / warps));
+    const int per_block = block_per_node ? 1 : warps;
+    const int blocks = std::max(1, std::min(4096, (count + per_block - 1) / per_block));
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess)
-        e = launch_propagate(h->W, P.stage_words > 0, P, blocks, warps * 32, smem, h->stream);
+        e = launch_propagate(h->W, P.stage_words > 0, P, blocks, warps * 32, smem, h->stream,
+                             block_per_node);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dom_out, h->ws + L.o_qrec, sw * count, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(failed, h->ws + L.o_sols, 4 * (size_t)count, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    // statistics of the call: one node per state, the failed ones, the kernel's device time
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    cudaGetLastError();
+    int64_t nf = 0;
+    for (int32_t k = 0; k < count; ++k) nf += failed[k] != 0;
+    h->stats = csp_stats_t{};
+    h->stats.nodes = (uint64_t)count;
+    h->stats.fails = (uint64_t)nf;
+    h->stats.ms = ms;
+    h->stats.blocks = blocks;
+    h->stats.workers = block_per_node ? blocks : blocks * warps;
+    h->stats.h2d_bytes = (int64_t)B.size() * 4 + (int64_t)sw * count;
+    h->stats.d2h_bytes = (int64_t)(sw + 4) * count;
+    return CSP_OK;
 }
 
 int csp_stats(const csp_t *h, csp_stats_t *out) {
@@ -1106,8 +1136,8 @@ int csp_batch_create_roots(csp_batch_t **out, csp_t *base, int32_t count, const 
 
 int csp_batch_set_tiling(csp_batch_t *b, const csp_tiling *t) {
     if (!b) return CSP_EINVAL;
-    csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0};
-    if (nt.queue_records & (nt.queue_records - 1)) return CSP_EINVAL;
+    csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0, 0};
+    if (!tiling_ok(nt)) return CSP_EINVAL;
     b->tiling = nt;
     b->uploaded = false;
     drop_graph(b);

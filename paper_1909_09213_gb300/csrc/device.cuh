@@ -791,6 +791,137 @@ __device__ bool fixpoint(const IV<ST> &I, int dom, int chg, int evs, bool full,
     }
 }
 
+// ------------------------------------------------------------------ one node, many warps
+// The fixpoint of one node computed by every warp of the block (constraint-parallel
+// propagation of a node too large for one warp: the constraints of each kind are grouped,
+// as Section 2.2 groups them, and shared out among the warps): in each round every warp reads
+// the same event set and takes its share of the work of each kind (the fixed variables of
+// int_ne by index, the 32-table chunks of one-word tables, rows, groups and multi-word tables
+// by index); domain writes stay atomicAnd, so concurrent warps only ever clear bits; a block
+// barrier ends the round.  Every thread of the block calls it.  Returns true (in every
+// thread) when some domain became empty.
+template <int W, bool ST>
+__device__ bool fixpoint_block(const IV<ST> &I, int dom, int chg, int evs, bool full,
+                               unsigned long long &evals, unsigned long long &rounds) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int n = I.n, NW = I.NW;
+    if (I.flags & FLAG_TRIVIAL_FAIL) return true;
+    if (full) {
+        for (int c = threadIdx.x; c < NW; c += blockDim.x) {
+            const int rem = n - (c << 5);
+            SM[chg + c] = rem >= 32 ? FULLMASK : ((1u << rem) - 1u);
+        }
+        const int nun = (int)I.w(H_N_UN), un = (int)I.w(H_OFF_UN);
+        for (int i = threadIdx.x; i < nun; i += blockDim.x) {
+            const uint32_t u = I.w(un + i);
+            const int x = (int)(u & 0xffffu), bit = (int)(u >> 16);
+            atomicAnd(&SM[dom + x * W + (bit >> 5)], ~(1u << (bit & 31)));
+        }
+    }
+    __syncthreads();
+    const int adj_start = (int)I.w(H_OFF_ADJ_START), adj = (int)I.w(H_OFF_ADJ);
+    const int n_tab = (int)I.w(H_N_TAB);
+    const int n_lin = (int)I.w(H_N_LIN), n_ad = (int)I.w(H_N_AD), n_adb = (int)I.w(H_N_ADB);
+    const bool has_ne = I.w(H_N_NE) != 0u;
+    for (;;) {
+        // 1. this round's events (every thread reads them after the barrier)
+        for (int c = threadIdx.x; c < NW; c += blockDim.x) {
+            SM[evs + c] = SM[chg + c];
+            SM[chg + c] = 0u;
+        }
+        __syncthreads();
+        bool any_ev = false;
+        for (int c = 0; c < NW; ++c) any_ev |= SM[evs + c] != 0u;
+        if (!any_ev) return false;
+        rounds++;
+        // 2. empty and fixed variables among the events (each warp computes the fixed set)
+        uint32_t fxw = 0;
+        bool fail = false;
+        for (int c = 0; c < NW; ++c) {
+            const uint32_t e = SM[evs + c];
+            if (!e) continue;
+            const int v = (c << 5) + lane;
+            const bool mine = (e >> lane) & 1u;
+            const int pc = mine ? dom_popc<W>(dom + v * W) : 2;
+            fail |= pc == 0;
+            const uint32_t f = __ballot_sync(FULLMASK, mine && pc == 1);
+            if (lane == c) fxw = f;
+        }
+        // 3. int_ne: the fixed variables v with v mod nwarps == warp
+        if (has_ne && !__any_sync(FULLMASK, fail)) {
+            for (int c = 0; c < NW; ++c) {
+                uint32_t f = __shfl_sync(FULLMASK, fxw, c);
+                while (f) {
+                    const int v = (c << 5) + __ffs(f) - 1;
+                    f &= f - 1;
+                    if (v % nwarps != warp) continue;
+                    const int val = __shfl_sync(FULLMASK, dom_min<W>(dom + v * W), 0);
+                    if (val < 0) continue;                  // emptied this round: caught next
+                    const int e0 = (int)I.w(adj_start + v), e1 = (int)I.w(adj_start + v + 1);
+                    for (int e = e0 + lane; e < e1; e += 32) {
+                        const uint32_t ent = I.w(adj + e);
+                        const int t = (int)(ent & 0xffffu);
+                        const int tb = val + (int)(int16_t)(ent >> 16);
+                        if ((unsigned)tb < (unsigned)(32 * W)) {
+                            const uint32_t m = 1u << (tb & 31);
+                            const uint32_t old = atomicAnd(&SM[dom + t * W + (tb >> 5)], ~m);
+                            if (old & m) mark_changed(chg, t);
+                        }
+                    }
+                    if (lane == 0) evals++;
+                }
+            }
+        }
+        // 4. tables whose x or y changed: 32-table chunks (one word) or tables (wider) by warp
+        if (n_tab && !__any_sync(FULLMASK, fail)) {
+            const int tab = (int)I.w(H_OFF_TAB);
+            for (int base = 0; base < n_tab && !fail; base += 32) {
+                const int t = base + lane;
+                bool ex = false, ey = false;
+                if (t < n_tab) {
+                    ex = ev_has(evs, (int)I.w(tab + 4 * t));
+                    ey = ev_has(evs, (int)I.w(tab + 4 * t + 1));
+                }
+                uint32_t sm = __ballot_sync(FULLMASK, ex || ey);
+                while (sm) {
+                    const int tt = base + __ffs(sm) - 1;
+                    sm &= sm - 1;
+                    if (tt % nwarps != warp) continue;
+                    if (lane == 0) evals++;
+                    if (revise_table<W, ST>(I, dom, chg, tt)) {
+                        fail = true;
+                        break;
+                    }
+                }
+            }
+        }
+        // 5. rows, 6. value-elimination groups, 7. bounds-consistent groups, by index
+        if (n_lin && !__any_sync(FULLMASK, fail)) {
+            fail = for_scheduled<ST>(I, evs, (int)I.w(H_OFF_LIN_MASK), (int)I.w(H_LIN_MW), [&](int r) {
+                if (r % nwarps != warp) return false;
+                if (lane == 0) evals++;
+                return revise_lin<W, ST>(I, dom, chg, r);
+            });
+        }
+        if (n_ad && !__any_sync(FULLMASK, fail)) {
+            fail = for_scheduled<ST>(I, evs, (int)I.w(H_OFF_AD_MASK), (int)I.w(H_AD_MW), [&](int g) {
+                if (g % nwarps != warp) return false;
+                if (lane == 0) evals++;
+                return revise_alldiff<W, ST>(I, dom, chg, g);
+            });
+        }
+        if (n_adb && !__any_sync(FULLMASK, fail)) {
+            fail = for_scheduled<ST>(I, evs, (int)I.w(H_OFF_ADB_MASK), (int)I.w(H_ADB_MW), [&](int g) {
+                if (g % nwarps != warp) return false;
+                if (lane == 0) evals++;
+                return revise_alldiff_bc<W, ST>(I, dom, chg, g);
+            });
+        }
+        fail = __any_sync(FULLMASK, fail);
+        if (__syncthreads_or(fail ? 1 : 0)) return true;
+    }
+}
+
 // First-fail: the unfixed variable with the fewest values, lowest index on ties; -1 when
 // every variable is fixed.
 template <int W>

@@ -10,7 +10,7 @@ namespace cubics {
     cudaError_t launch_search_ext_w##WW(bool, const SearchArgs &, int, int, size_t,          \
                                         cudaStream_t);                                       \
     cudaError_t occupancy_ext_w##WW(bool, int, size_t, int *);                               \
-    cudaError_t launch_prop_w##WW(bool, const PropArgs &, int, int, size_t, cudaStream_t);
+    cudaError_t launch_prop_w##WW(bool, const PropArgs &, int, int, size_t, cudaStream_t, bool);
 CUBICS_DECLARE_WIDTH(1)
 CUBICS_DECLARE_WIDTH(2)
 CUBICS_DECLARE_WIDTH(4)
@@ -57,13 +57,14 @@ cudaError_t occupancy_search(int W, bool staged, int kind, int threads, size_t s
 #undef CUBICS_CASE
 }
 
+// block_per_node: one block per state, every warp of it on that state's constraints
 cudaError_t launch_propagate(int W, bool staged, const PropArgs &P, int blocks, int threads,
-                             size_t smem, cudaStream_t st) {
+                             size_t smem, cudaStream_t st, bool block_per_node) {
     switch (W) {
-    case 1: return launch_prop_w1(staged, P, blocks, threads, smem, st);
-    case 2: return launch_prop_w2(staged, P, blocks, threads, smem, st);
-    case 4: return launch_prop_w4(staged, P, blocks, threads, smem, st);
-    case 8: return launch_prop_w8(staged, P, blocks, threads, smem, st);
+    case 1: return launch_prop_w1(staged, P, blocks, threads, smem, st, block_per_node);
+    case 2: return launch_prop_w2(staged, P, blocks, threads, smem, st, block_per_node);
+    case 4: return launch_prop_w4(staged, P, blocks, threads, smem, st, block_per_node);
+    case 8: return launch_prop_w8(staged, P, blocks, threads, smem, st, block_per_node);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1139,6 +1139,31 @@ __global__ void __launch_bounds__(256) propagate_kernel(PropArgs P) {
     }
 }
 
+// One fixpoint per state, a whole block per state (constraint-parallel propagation of one
+// node by all the block's warps).  Shared memory: the staged instance, then the state
+// (S words, rounded to 4), its changed set and event set (32 words each).
+template <int W, bool ST>
+__global__ void __launch_bounds__(1024) propagate_block_kernel(PropArgs P) {
+    if (ST) stage_instance(P.inst);
+    __syncthreads();
+    IV<ST> I;
+    I.load(P.inst);
+    const int S4 = (I.S + 3) & ~3;
+    const int dom = P.stage_words, chg = dom + S4, evs = chg + 32;
+    unsigned long long evals = 0, rounds = 0;
+    for (int s = blockIdx.x; s < P.count; s += gridDim.x) {
+        const uint32_t *src = P.din + (size_t)s * I.S;
+        for (int k = threadIdx.x; k < I.S; k += blockDim.x) SM[dom + k] = src[k];
+        __syncthreads();
+        const bool failed = fixpoint_block<W, ST>(I, dom, chg, evs, true, evals, rounds);
+        __syncthreads();
+        uint32_t *dst = P.dout + (size_t)s * I.S;
+        for (int k = threadIdx.x; k < I.S; k += blockDim.x) dst[k] = SM[dom + k];
+        if (threadIdx.x == 0) P.failed[s] = failed ? 1 : 0;
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ host launchers
 
 template <typename K>
@@ -1189,7 +1214,15 @@ cudaError_t occupancy_t(int threads, size_t smem, int *bps) {
 }
 
 template <int W, bool ST>
-cudaError_t launch_prop_t(const PropArgs &P, int blocks, int threads, size_t smem, cudaStream_t st) {
+cudaError_t launch_prop_t(const PropArgs &P, int blocks, int threads, size_t smem, cudaStream_t st,
+                          bool block_per_node) {
+    if (block_per_node) {
+        cudaError_t e = cudaFuncSetAttribute(propagate_block_kernel<W, ST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        propagate_block_kernel<W, ST><<<blocks, threads, smem, st>>>(P);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(propagate_kernel<W, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1214,9 +1247,9 @@ cudaError_t launch_prop_t(const PropArgs &P, int blocks, int threads, size_t sme
 #define CUBICS_DEFINE_WIDTH(WW)                                                              \
     CUBICS_DEFINE_SEARCH(WW, false, )                                                        \
     cudaError_t launch_prop_w##WW(bool st_, const PropArgs &P, int b, int t, size_t sm,     \
-                                  cudaStream_t s) {                                         \
-        return st_ ? launch_prop_t<WW, true>(P, b, t, sm, s)                                \
-                   : launch_prop_t<WW, false>(P, b, t, sm, s);                              \
+                                  cudaStream_t s, bool bpn) {                               \
+        return st_ ? launch_prop_t<WW, true>(P, b, t, sm, s, bpn)                           \
+                   : launch_prop_t<WW, false>(P, b, t, sm, s, bpn);                         \
     }
 
 #define CUBICS_DEFINE_WIDTH_EXT(WW) CUBICS_DEFINE_SEARCH(WW, true, _ext)

@@ -1,11 +1,13 @@
-"""Autotuner for the search kernel's launch shape.
+"""Autotuner for the search and propagation kernels' launch shapes.
 
 The occupancy trade of Section 2.3 (fewer threads per SM when the data cached in shared
 memory grows) becomes a measured choice: warps per block (workers sharing one instance's
 staged constraints and one work queue), search levels kept in shared memory per worker, and
 queue capacity.  Candidates are timed on a calibration subset with CUDA events (the
 library's own launch timing); the fastest is cached in a JSON file keyed by GPU, domain
-width and a size bucket.  A tiling changes only speed, never results.
+width and a size bucket.  For propagation alone the tuned axis is the number of threads
+per node: a warp per domain state, or a whole block per state (tune_propagate).  A tiling
+changes only speed, never results.
 """
 from __future__ import annotations
 
@@ -105,6 +107,44 @@ def tune_single(model, mode=K.CSP_ALL, reps=2, use_cache=True, verbose=False):
             print(f"tune single {cand}: {best:.2f} ms", flush=True)
     best_ms, best = min(results, key=lambda r: r[0])
     entry = {"tiling": best, "ms": best_ms, "candidates": [[r[0], r[1]] for r in results]}
+    if use_cache:
+        cache[key] = entry
+        _store(cache)
+    return K.tiling(**best), entry
+
+
+PROPAGATE_CANDIDATES = [dict(threads_per_node=t) for t in (32, 64, 128, 256, 512, 1024)]
+
+
+def tune_propagate(model, states, reps=2, use_cache=True, verbose=False):
+    """Threads per node for csp_propagate on states like `states` ((count, n*W) uint32): a
+    warp per state, or a block of 64..1024 threads per state with the constraints shared out
+    among its warps; each candidate timed on the states themselves (wall time of the call,
+    copies included).  A choice of speed only: every candidate reaches the same fixpoints."""
+    import time
+    key = f"{_gpu_name()}|propagate|{size_bucket([model])}|{model.name}|{len(states)}"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return K.tiling(**cache[key]["tiling"]), cache[key]
+    results = []
+    for cand in PROPAGATE_CANDIDATES:
+        p = K.Csp(model)
+        p.set_tiling(K.tiling(**cand))
+        best = None
+        try:
+            for _ in range(reps + 1):
+                t0 = time.perf_counter()
+                p.propagate(states)
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+        except K.CspError:
+            continue
+        results.append((best * 1e3, cand))
+        if verbose:
+            print(f"tune propagate {cand}: {best * 1e3:.2f} ms", flush=True)
+    best_ms, best = min(results, key=lambda r: r[0])
+    entry = {"tiling": best, "ms": best_ms, "states": len(states),
+             "candidates": [[r[0], r[1]] for r in results]}
     if use_cache:
         cache[key] = entry
         _store(cache)
