@@ -77,6 +77,16 @@ typedef struct {
                                  each kind (constraint-parallel propagation of one node too
                                  large for a warp, Section 2.2's grouping by kind); a search
                                  plan with it is CSP_EINVAL */
+    int32_t split_depth;      /* all-solution search of one problem (csp_solve / csp_launch):
+                                 k = 1..8: the first k levels are expanded on the device (one
+                                 fixpoint and one expansion kernel per level; csp_launch then
+                                 waits for the device between levels) and the subtrees below
+                                 them are solved like a batch, each block's warps sharing one
+                                 subtree through the block's own queue; 0 = the library's
+                                 choice (3); -1 = all workers share one queue of the whole
+                                 tree.  Same counts and hashes either way; no effect on
+                                 first-solution search, partitions, the learned brancher
+                                 (CSP_BR_LEARNED) or csp_solve_noalloc */
 } csp_tiling;
 
 typedef struct {
@@ -99,6 +109,8 @@ typedef struct {
     int64_t d2h_bytes;       /* device-to-host bytes of the last collect */
     uint64_t wait_ns;        /* summed over workers: time spent waiting for work */
     uint64_t rounds;         /* fixpoint rounds (propagation passes over the changed scopes) */
+    double kernel_ms;        /* device time of the search kernel alone (ms also covers the
+                                level expansion of a split search) */
 } csp_stats_t;
 
 typedef struct {

@@ -151,6 +151,27 @@ struct SearchArgs {
     float *logbuf;            // log entries of 17 floats: 16 features, log2 subtree nodes
     unsigned long long *log_count;
     long long log_cap;
+    const uint32_t *roots;    // batch: root domains of instance i at roots + i * S (all
+                              // instances sharing one block); NULL: each block's own roots
+    int32_t global_limits;    // batch: the node limit counts all instances together and stops
+                              // the launch (the instances are parts of one search)
+    int32_t pad_args;
+};
+
+// One level of the depth-k split of a single problem (expand_level_kernel): propagated
+// states in, their first-fail children and fully fixed states out.  ctr: [0] children
+// written to `next`, [1] fully fixed states written to `units`, [2] nodes (branching or
+// failed states), [3] failed states, [4] set when a buffer would overflow.
+struct ExpandArgs {
+    const uint32_t *inst;
+    const uint32_t *states;
+    const int32_t *failed;
+    int32_t count;
+    uint32_t *next;
+    int64_t next_cap;
+    uint32_t *units;
+    int64_t units_cap;
+    unsigned long long *ctr;
 };
 
 struct PropArgs {

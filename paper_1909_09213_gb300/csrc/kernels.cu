@@ -10,7 +10,8 @@ namespace cubics {
     cudaError_t launch_search_ext_w##WW(bool, const SearchArgs &, int, int, size_t,          \
                                         cudaStream_t);                                       \
     cudaError_t occupancy_ext_w##WW(bool, int, size_t, int *);                               \
-    cudaError_t launch_prop_w##WW(bool, const PropArgs &, int, int, size_t, cudaStream_t, bool);
+    cudaError_t launch_prop_w##WW(bool, const PropArgs &, int, int, size_t, cudaStream_t, bool); \
+    cudaError_t launch_expand_w##WW(const ExpandArgs &, int, cudaStream_t);
 CUBICS_DECLARE_WIDTH(1)
 CUBICS_DECLARE_WIDTH(2)
 CUBICS_DECLARE_WIDTH(4)
@@ -65,6 +66,16 @@ cudaError_t launch_propagate(int W, bool staged, const PropArgs &P, int blocks, 
     case 2: return launch_prop_w2(staged, P, blocks, threads, smem, st, block_per_node);
     case 4: return launch_prop_w4(staged, P, blocks, threads, smem, st, block_per_node);
     case 8: return launch_prop_w8(staged, P, blocks, threads, smem, st, block_per_node);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_expand(int W, const ExpandArgs &E, int blocks, cudaStream_t st) {
+    switch (W) {
+    case 1: return launch_expand_w1(E, blocks, st);
+    case 2: return launch_expand_w2(E, blocks, st);
+    case 4: return launch_expand_w4(E, blocks, st);
+    case 8: return launch_expand_w8(E, blocks, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -250,7 +250,7 @@ struct Worker {
                 atomicAdd(&T->usum[pbin], (unsigned long long)(tick - credited));
                 credited = tick;
             }
-            if (SA.node_limit > 0 && SA.batch) {
+            if (SA.node_limit > 0 && SA.batch && !SA.global_limits) {
                 const unsigned long long tot = atomicAdd(&T->progress, 64ull) + 64ull;
                 if ((long long)tot >= SA.node_limit) atomicCAS(&T->found, 0, 2);
             } else if (SA.node_limit > 0) {
@@ -1029,7 +1029,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
         __syncwarp();
         if (own && warp == 0) {
             // root record: the instance's root domains, nothing to try yet, var = -1
-            const uint32_t *root = ib + ib[H_OFF_ROOT];
+            const uint32_t *root = SA.roots ? SA.roots + (size_t)i * wk.S : ib + ib[H_OFF_ROOT];
             for (int k = lane; k < wk.R; k += 32)
                 SM[wk.slots + k] = k < wk.S ? root[k] : (k == wk.S + W ? 0xffffffffu : 0u);
             if (lane == 0) {
@@ -1164,6 +1164,76 @@ __global__ void __launch_bounds__(1024) propagate_block_kernel(PropArgs P) {
     }
 }
 
+// One level of the depth-k split of a single problem, a warp per propagated state: a failed
+// state is a node and a fail; a state with every variable fixed is a unit as it stands (its
+// node is counted when the unit is searched); any other state is a node whose first-fail
+// variable (fewest values, lowest index) gives one child per value, ascending, written to
+// `next` at slots reserved with an atomic add (the children of different states interleave
+// in any order).  A reservation beyond a buffer sets the overflow counter and writes nothing.
+template <int W>
+__global__ void __launch_bounds__(256) expand_level_kernel(ExpandArgs E) {
+    const int lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int n = (int)E.inst[H_N], S = (int)E.inst[H_S];
+    for (int s = warp; s < E.count; s += nwarps) {
+        const uint32_t *st = E.states + (size_t)s * S;
+        if (E.failed[s]) {
+            if (lane == 0) {
+                atomicAdd(&E.ctr[2], 1ull);
+                atomicAdd(&E.ctr[3], 1ull);
+            }
+            continue;
+        }
+        unsigned best = 0xffffffffu;
+        for (int v = lane; v < n; v += 32) {
+            int pc = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) pc += __popc(st[v * W + k]);
+            if (pc > 1) best = min(best, ((unsigned)pc << 16) | (unsigned)v);
+        }
+        best = __reduce_min_sync(FULLMASK, best);
+        if (best == 0xffffffffu) {
+            unsigned long long slot = 0;
+            if (lane == 0) slot = atomicAdd(&E.ctr[1], 1ull);
+            slot = __shfl_sync(FULLMASK, slot, 0);
+            if ((long long)slot < E.units_cap) {
+                for (int k = lane; k < S; k += 32) E.units[(size_t)slot * S + k] = st[k];
+            } else if (lane == 0) {
+                atomicExch(&E.ctr[4], 1ull);
+            }
+            continue;
+        }
+        const int y = (int)(best & 0xffffu), c = (int)(best >> 16);
+        unsigned long long base = 0;
+        if (lane == 0) {
+            atomicAdd(&E.ctr[2], 1ull);
+            base = atomicAdd(&E.ctr[0], (unsigned long long)c);
+        }
+        base = __shfl_sync(FULLMASK, base, 0);
+        if ((long long)(base + c) > E.next_cap) {
+            if (lane == 0) atomicExch(&E.ctr[4], 1ull);
+            continue;
+        }
+        long long j = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint32_t m = st[y * W + w];
+            while (m) {
+                const uint32_t bit = m & (~m + 1u);
+                m ^= bit;
+                uint32_t *ch = E.next + (size_t)(base + j) * S;
+                for (int k = lane; k < S; k += 32) {
+                    uint32_t val = st[k];
+                    if (k >= y * W && k < (y + 1) * W) val = k == y * W + w ? bit : 0u;
+                    ch[k] = val;
+                }
+                ++j;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host launchers
 
 template <typename K>
@@ -1246,6 +1316,10 @@ cudaError_t launch_prop_t(const PropArgs &P, int blocks, int threads, size_t sme
 
 #define CUBICS_DEFINE_WIDTH(WW)                                                              \
     CUBICS_DEFINE_SEARCH(WW, false, )                                                        \
+    cudaError_t launch_expand_w##WW(const ExpandArgs &E, int blocks, cudaStream_t s) {       \
+        expand_level_kernel<WW><<<blocks, 256, 0, s>>>(E);                                  \
+        return cudaGetLastError();                                                          \
+    }                                                                                       \
     cudaError_t launch_prop_w##WW(bool st_, const PropArgs &P, int b, int t, size_t sm,     \
                                   cudaStream_t s, bool bpn) {                               \
         return st_ ? launch_prop_t<WW, true>(P, b, t, sm, s, bpn)                           \

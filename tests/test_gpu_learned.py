@@ -65,6 +65,19 @@ def test_learned_tree_does_not_depend_on_work_sharing():
     assert one["solutions"] == ff["solutions"] == 2680
 
 
+@pytest.mark.parametrize("split", [-1, 3, 8])
+def test_learned_order_ignores_the_split_depth(split):
+    # the device expansion of a split branches first-fail, so the learned brancher always
+    # searches the whole tree through one queue: the tree is the same at every split depth
+    w = _weights(6)
+    for m in _models():
+        ref, ref_sols = _solve(m, K.CSP_BR_LEARNED, w, K.tiling(split_depth=-1))
+        st, sols = _solve(m, K.CSP_BR_LEARNED, w, K.tiling(split_depth=split))
+        for k in ("nodes", "fails", "solutions", "sol_hash_sum", "sol_hash_xor"):
+            assert st[k] == ref[k], (m.name, split, k)
+        assert sorted(map(tuple, sols.tolist())) == sorted(map(tuple, ref_sols.tolist()))
+
+
 def test_nan_network_falls_back_to_first_fail():
     w = _weights(4)
     w[M.N_PARAMS - 1] = 0x7FC0                      # b3 = NaN: every score is NaN

@@ -171,9 +171,14 @@ def test_propagate_empty_and_singletons():
 # ----------------------------------------------------------------------------- search
 
 TILINGS = {
-    "auto": None,
-    "one-worker": K.tiling(blocks=1, warps_per_block=1),
-    "spilling": K.tiling(blocks=3, warps_per_block=4, smem_levels=2, queue_records=8),
+    "auto": None,                          # all-solution search split at depth 3 by default
+    "shared": K.tiling(split_depth=-1),    # one queue shared by every worker
+    "one-worker": K.tiling(blocks=1, warps_per_block=1, split_depth=-1),
+    "spilling": K.tiling(blocks=3, warps_per_block=4, smem_levels=2, queue_records=8, split_depth=-1),
+    # all-solution search split at depth k into units solved by per-block teams
+    "split1": K.tiling(split_depth=1),
+    "split3": K.tiling(split_depth=3, warps_per_block=4),
+    "split8": K.tiling(split_depth=8, blocks=5, warps_per_block=2, smem_levels=2),
 }
 
 
@@ -295,8 +300,10 @@ def test_search_random_ne_one_word(n, dmax, m):
 
 def test_search_spill_heavy_deep_stack():
     # 12-queens with 2 shared-memory levels per worker: most levels live in global memory
-    st = search_parity(I.queens(12), K.tiling(blocks=4, warps_per_block=8, smem_levels=2), cap=10)
-    assert st["spills"] > 0
+    for split in (-1, 0):
+        st = search_parity(I.queens(12), K.tiling(blocks=4, warps_per_block=8, smem_levels=2,
+                                                  split_depth=split), cap=10)
+        assert st["spills"] > 0
 
 
 def test_first_mode_status_and_validity():
@@ -340,6 +347,7 @@ def oracle_reference(N):
 def test_queens_full_size_against_oracle_reference(N):
     ref = oracle_reference(N)
     p = K.Csp(I.queens(N))
+    p.set_tiling(K.tiling(split_depth=-1))         # one shared queue (split: further below)
     rc, st, _ = p.solve(K.CSP_ALL, 0)
     assert rc == 0 and st["solutions"] == queens_count(N) == ref["solutions"]
     assert (st["nodes"], st["fails"]) == (ref["nodes"], ref["fails"])
@@ -353,12 +361,15 @@ def test_queens_14_full_size():
 
 
 def test_queens_16_full_size_and_sampled_subtrees():
-    """16-queens in the benchmark's launch shape: the published count; nodes, fails and the
-    solution hash of sampled subtrees (x0, x1 fixed) against the oracle."""
-    p = K.Csp(I.queens(16))
-    rc, st, _ = p.solve(K.CSP_ALL, 0)
-    assert rc == 0 and st["solutions"] == queens_count(16)
-    assert st["steals"] > 0
+    """16-queens in the benchmark's launch shape (one shared queue) and split: the published
+    count; nodes, fails and the solution hash of sampled subtrees (x0, x1 fixed) against the
+    oracle."""
+    for split in (-1, 0):
+        p = K.Csp(I.queens(16))
+        p.set_tiling(K.tiling(split_depth=split))
+        rc, st, _ = p.solve(K.CSP_ALL, 0)
+        assert rc == 0 and st["solutions"] == queens_count(16)
+        assert st["steals"] > 0
     for (a, b) in [(0, 2), (7, 3)]:
         m = I.queens(16)
         m.removed += [(0, v) for v in range(16) if v != a] + [(1, v) for v in range(16) if v != b]
@@ -410,11 +421,78 @@ def test_tree_cut_at_depth_k_sums_to_the_whole(depth, nparts):
         assert any(found) == (whole["solutions"] > 0), m.name
 
 
+@pytest.mark.parametrize("N,depth", [(14, 3), (16, 3), (16, 4)])
+def test_split_full_size_against_oracle_reference(N, depth):
+    """The benchmark's trees split at depth k: nodes, fails, solutions and both hashes equal
+    the oracle's full-size run."""
+    ref = oracle_reference(N)
+    p = K.Csp(I.queens(N))
+    p.set_tiling(K.tiling(split_depth=depth))
+    rc, st, _ = p.solve(K.CSP_ALL, 0)
+    assert rc == 0
+    assert (st["nodes"], st["fails"], st["solutions"], st["sol_hash_sum"], st["sol_hash_xor"]) == (
+        ref["nodes"], ref["fails"], ref["solutions"], ref["hash_sum"], ref["hash_xor"])
+
+
+@pytest.mark.parametrize("tname", ["split1", "split3"])
+def test_split_wide_domains_and_every_kind(tname):
+    for m in [strided_queens(9, 31), strided_queens(8, 13, alldiff=True, rows=True),
+              pooled_wide_model(1003, 250), mixed_model(101, 40, 5),
+              I.model_rb(I.seed_for(I.CFG_RB, 902), 12, 6)]:
+        search_parity(m, TILINGS[tname], cap=20000)
+
+
+def test_split_repeated_launches_and_stored_solutions():
+    """One upload, several launches: each launch restarts the split from the root; the
+    stored solutions are the oracle's."""
+    m = I.queens(9)
+    r = O.solve(O.OracleModel(m), cap=400, variant=1)
+    p = K.Csp(m)
+    p.set_tiling(K.tiling(split_depth=2))
+    p.bind(K.CSP_ALL, 400)
+    p.upload(K.CSP_ALL, 400)
+    for _ in range(3):
+        sols = np.zeros((400, 9), np.int32)
+        p.launch()
+        assert p.collect(sols) == 0
+        st = p.stats()
+        assert (st["nodes"], st["fails"], st["solutions"]) == (r.nodes, r.fails, r.solutions)
+        assert sorted_rows(sols[:st["stored"]]) == sorted_rows(r.sols)
+
+
+def test_split_limits_are_global_and_partitions_unsplit():
+    p = K.Csp(I.queens(12))
+    p.set_tiling(K.tiling(split_depth=3, blocks=2, warps_per_block=2))
+    rc, st, _ = p.solve(K.CSP_ALL, 0, K.limits(node_limit=5_000))
+    assert rc == K.CSP_ELIMIT
+    # a partitioned handle keeps the shared-queue search: the parts still sum to the whole
+    from paper_1909_09213_gb300 import shard
+    m = I.queens(10)
+    rc, whole, _ = K.Csp(m).solve(K.CSP_ALL, 0)
+    parts = []
+    for part in range(3):
+        q = K.Csp(m)
+        q.set_tiling(K.tiling(split_depth=3))
+        q.set_partition(part, 3)
+        rc, st, _ = q.solve(K.CSP_ALL, 0)
+        assert rc == 0
+        parts.append(st)
+    got = shard.combine(parts)
+    assert all(got[k] == whole[k] for k in shard.FIELDS)
+    # first-solution search is not split
+    q = K.Csp(I.queens(10))
+    q.set_tiling(K.tiling(split_depth=3))
+    rc, st, sols = q.solve(K.CSP_FIRST)
+    assert rc == 0 and st["solutions"] == 1 and O.check_solution(O.OracleModel(I.queens(10)), sols[0])
+
+
 # ----------------------------------------------------------------------------- limits, errors
 
-def test_node_limit():
+@pytest.mark.parametrize("split", [-1, 0])
+def test_node_limit(split):
     p = K.Csp(I.queens(11))
-    p.set_tiling(K.tiling(blocks=1, warps_per_block=2))      # limits are checked every 64 nodes
+    # limits are checked every 64 nodes
+    p.set_tiling(K.tiling(blocks=1, warps_per_block=2, split_depth=split))
     rc, st, _ = p.solve(K.CSP_ALL, 0, K.limits(node_limit=200))
     assert rc == K.CSP_ELIMIT and st["nodes"] >= 200
 
@@ -422,6 +500,7 @@ def test_node_limit():
 def test_wait_limit_returns_timeout():
     # no worker ever donates, so every idle worker waits until the limit runs out
     p = K.Csp(I.queens(13))
+    p.set_tiling(K.tiling(split_depth=-1))                  # one queue for the whole tree
     rc, st, _ = p.solve(K.CSP_ALL, 0, K.limits(wait_limit_ns=20_000_000, flags=K.CSP_F_NO_DONATE))
     assert rc == K.CSP_ETIMEOUT
     rc, st, _ = p.solve(K.CSP_ALL, 0)                       # the context is still usable
