@@ -111,6 +111,9 @@ typedef struct {
     uint64_t rounds;         /* fixpoint rounds (propagation passes over the changed scopes) */
     double kernel_ms;        /* device time of the search kernel alone (ms also covers the
                                 level expansion of a split search) */
+    int64_t units;           /* subtrees the last search solved: those below the expanded
+                                levels of a split search, else 1; a batch: its problems;
+                                0 after csp_propagate */
 } csp_stats_t;
 
 typedef struct {

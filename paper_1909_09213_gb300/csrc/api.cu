@@ -1001,6 +1001,7 @@ int csp_collect(csp_t *h, int32_t *sol_out) {
     fill_stats(&h->stats, g, stored);
     h->stats.ms = ms;
     h->stats.kernel_ms = kms;
+    h->stats.units = P.split ? h->split_units : 1;
     h->stats.status = g.status;
     h->stats.d2h_bytes = d2h;
     return g.status;
@@ -1447,6 +1448,7 @@ int csp_batch_collect(csp_batch_t *b, csp_result *out, int32_t *sol) {
     fill_stats(&b->stats, g, 0);
     b->stats.ms = ms;
     b->stats.kernel_ms = ms;
+    b->stats.units = (int64_t)b->hs.size();
     b->stats.status = g.status;
     b->stats.h2d_bytes = b->pending_h2d;
     b->pending_h2d = 0;
@@ -1568,6 +1570,8 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
     if (e != cudaSuccess) return cuda_status(e);
     fill_stats(&h->stats, g, stored);
     h->stats.ms = 0.0;
+    h->stats.kernel_ms = 0.0;
+    h->stats.units = 1;
     h->stats.status = g.status;
     h->stats.workers = P.shape.blocks * P.shape.warps;
     h->stats.blocks = P.shape.blocks;

@@ -45,7 +45,7 @@ class csp_stats_t(C.Structure):
                 ("max_depth", C.c_int32), ("status", C.c_int32), ("ms", C.c_double),
                 ("stored", C.c_int64), ("workers", C.c_int32), ("blocks", C.c_int32),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("wait_ns", C.c_uint64),
-                ("rounds", C.c_uint64), ("kernel_ms", C.c_double)]
+                ("rounds", C.c_uint64), ("kernel_ms", C.c_double), ("units", C.c_int64)]
 
 
 class csp_result(C.Structure):

@@ -343,11 +343,13 @@ def oracle_reference(N):
     pytest.skip(f"no oracle reference for N={N}")
 
 
-@pytest.mark.parametrize("N", [14, 16])
-def test_queens_full_size_against_oracle_reference(N):
+@pytest.mark.parametrize("split", [-1, 0])
+@pytest.mark.parametrize("N", [14, 15, 16])
+def test_queens_full_size_against_oracle_reference(N, split):
+    # one shared queue, and the default split of the first levels
     ref = oracle_reference(N)
     p = K.Csp(I.queens(N))
-    p.set_tiling(K.tiling(split_depth=-1))         # one shared queue (split: further below)
+    p.set_tiling(K.tiling(split_depth=split))
     rc, st, _ = p.solve(K.CSP_ALL, 0)
     assert rc == 0 and st["solutions"] == queens_count(N) == ref["solutions"]
     assert (st["nodes"], st["fails"]) == (ref["nodes"], ref["fails"])
@@ -425,6 +427,7 @@ def test_tree_cut_at_depth_k_sums_to_the_whole(depth, nparts):
 def test_split_full_size_against_oracle_reference(N, depth):
     """The benchmark's trees split at depth k: nodes, fails, solutions and both hashes equal
     the oracle's full-size run."""
+    from paper_1909_09213_gb300 import shard
     ref = oracle_reference(N)
     p = K.Csp(I.queens(N))
     p.set_tiling(K.tiling(split_depth=depth))
@@ -432,6 +435,14 @@ def test_split_full_size_against_oracle_reference(N, depth):
     assert rc == 0
     assert (st["nodes"], st["fails"], st["solutions"], st["sol_hash_sum"], st["sol_hash_xor"]) == (
         ref["nodes"], ref["fails"], ref["solutions"], ref["hash_sum"], ref["hash_xor"])
+    # the subtrees solved: the same cut made on the host from csp_propagate's fixpoints
+    n, W = p.layout()[:2]
+    units, nodes, fails = shard.split_units(p.propagate, p.root_domains().ravel(), n, W, depth)
+    assert st["units"] == len(units)
+    q = K.Csp(I.queens(N))
+    q.set_tiling(K.tiling(split_depth=-1))
+    rc, st1, _ = q.solve(K.CSP_ALL, 0)
+    assert rc == 0 and st1["units"] == 1 and st1["nodes"] == st["nodes"]
 
 
 @pytest.mark.parametrize("tname", ["split1", "split3"])

@@ -83,6 +83,20 @@ def test_queens_12_count():
     assert O.solve(om).solutions == 14200
 
 
+def test_queens_full_size_oracle_rows():
+    # the stored full-size oracle searches (N = 14..16, written by the oracle alone) against
+    # the published counts, and the shape of a d-way tree: every internal node has at least
+    # two children, so leaves (fails + solutions) < nodes < 2 * leaves; 12 bytes per wake
+    counts = {r[0]: r[1] for r in _rows("queens_counts.txt")}
+    rows = _rows("queens_oracle.txt")
+    assert sorted(r[0] for r in rows) == [14, 15, 16]
+    for N, nodes, fails, sols, _hs, _hx, evals, work in rows:
+        assert sols == counts[N]
+        leaves = fails + sols
+        assert leaves < nodes < 2 * leaves
+        assert work == 12 * evals
+
+
 def test_queens_model_size():
     for N in (8, 14, 16):
         assert len(I.queens(N).ne) == 3 * N * (N - 1) // 2
