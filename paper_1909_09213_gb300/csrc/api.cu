@@ -68,6 +68,7 @@ struct Shape {
     int mlp_words = 0;     // staged brancher weights (learned ordering)
     int feat_words = 0;    // per-warp feature tile (learned ordering)
     int list_words = 0;    // per-warp scheduled-table list (one-word tables)
+    int hash_words = 0;    // per-warp deferred solution-hash buffer (register kernel)
     int warp_base = 0;     // shared-memory word where warp 0's area starts
     size_t smem = 0;
 };
@@ -88,11 +89,13 @@ int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batc
     if (s->warps > 32) return CSP_EINVAL;
     s->mlp_words = learned ? CSP_MLP_PACKED_WORDS : 0;
     s->feat_words = learned ? ((nmax + 15) & ~15) * 8 : 0;
+    s->hash_words = s->kind == KERN_REG ? HB_WORDS : 0;
     int lsm = t.smem_levels > 0 ? t.smem_levels : std::max(2, 6144 / R);
     lsm = std::max(2, std::min(lsm, depth));
     const int cons4 = (cons + 3) & ~3;
     auto bytes = [&](int l) {
-        return ((size_t)s->warps * (l * R + WS_WORDS + s->feat_words + s->list_words) + s->mlp_words) * 4;
+        return ((size_t)s->warps * (l * R + WS_WORDS + s->feat_words + s->list_words + s->hash_words) +
+                s->mlp_words) * 4;
     };
     // a power of two, so that a level's slot is its index masked: rounded up when the whole
     // stack was to fit (and still fits), down otherwise
@@ -157,7 +160,7 @@ struct Plan {
     // all-solution search split at depth k into units solved by per-block teams
     bool split = false;
     int64_t ucap = 0;                // capacity of the unit buffers (states)
-    size_t o_A = 0, o_B = 0, o_U = 0, o_failed = 0, o_ctr = 0, o_res = 0;
+    size_t o_A = 0, o_B = 0, o_U = 0, o_failed = 0, o_scan = 0, o_ctr = 0, o_res = 0;
     size_t bytes = 0;
 };
 
@@ -473,6 +476,7 @@ int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<ui
         p.o_B = c.take((size_t)(2 * p.ucap) * S4);
         p.o_U = c.take((size_t)p.ucap * S4);
         p.o_failed = c.take((size_t)(2 * p.ucap) * 4);
+        p.o_scan = c.take((size_t)(2 * p.ucap) * 8);
         p.o_ctr = c.take(8 * 8);
         p.bytes = c.off;
         *P = p;
@@ -507,6 +511,7 @@ void set_learned_args(SearchArgs &A, const Shape &s, bool learned, const uint8_t
     A.mlp_off = learned ? s.stage_words : -1;
     A.feat_words = s.feat_words;
     A.list_words = s.list_words;
+    A.hash_words = s.hash_words;
     A.warp_base = s.warp_base;
 }
 
@@ -848,7 +853,8 @@ int csp_upload(csp_t *h, int32_t mode, int64_t cap) {
 
 // The all-solution search split at depth k (csp_tiling.split_depth): the root is copied to
 // level buffer A; each of the first k levels is propagated in place and expanded into B
-// (children) and U (states with every variable fixed), the counters read back after each
+// (children) and U (states with every variable fixed), both in the order of their parents
+// (the units come out in depth-first order at every run), the counters read back after each
 // level; an expansion that would overflow a buffer is undone and its (propagated) level
 // becomes the units.  The units (A's states, then U's) are then solved as a batch whose
 // instances share the problem's block and take their roots from A, each block's warps
@@ -900,6 +906,7 @@ static cudaError_t split_launch(csp *h, const csp_limits *lim) {
         E.units = (uint32_t *)(w + P.o_U);
         E.units_cap = P.ucap;
         E.ctr = ctr;
+        E.off = (unsigned long long *)(w + P.o_scan);
         const int eblocks = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (count + 7) / 8));
         if (e == cudaSuccess) e = launch_expand(W, E, eblocks, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(cur, ctr, sizeof(cur), cudaMemcpyDeviceToHost, st);

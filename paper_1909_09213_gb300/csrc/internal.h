@@ -21,6 +21,13 @@ constexpr uint32_t FLAG_NE_REG = 4u;        // also one word per domain and n <=
                                             // can hold a node's domains in registers, one
                                             // variable per lane (offset masks at H_OFF_NEMASK)
 constexpr int WS_WORDS = 92;            // per-warp shared bookkeeping (events, counters)
+// Deferred solution hashing of the register kernel: up to HB_SOLS solutions of at most 32
+// one-byte values (offsets from lo0), HB_STRIDE words apart (8 words of values and one of
+// padding, so that neither the byte writes of one solution nor the lanes' reads of one word
+// each of different solutions meet in a bank)
+constexpr int HB_SOLS = 32;
+constexpr int HB_STRIDE = 9;
+constexpr int HB_WORDS = HB_SOLS * HB_STRIDE;
 // search kernel kinds
 constexpr int KERN_PLAIN = 0;           // first-fail, domains in shared memory
 constexpr int KERN_EXT = 1;             // learned brancher and/or subtree logging
@@ -155,13 +162,17 @@ struct SearchArgs {
                               // instances sharing one block); NULL: each block's own roots
     int32_t global_limits;    // batch: the node limit counts all instances together and stops
                               // the launch (the instances are parts of one search)
-    int32_t pad_args;
+    int32_t hash_words;       // per-warp words of the deferred solution-hash buffer (register
+                              // kernel: HB_SOLS solutions of HB_STRIDE words), else 0
 };
 
-// One level of the depth-k split of a single problem (expand_level_kernel): propagated
-// states in, their first-fail children and fully fixed states out.  ctr: [0] children
-// written to `next`, [1] fully fixed states written to `units`, [2] nodes (branching or
-// failed states), [3] failed states, [4] set when a buffer would overflow.
+// One level of the depth-k split of a single problem (expand_count_kernel,
+// expand_scan_kernel, expand_write_kernel): propagated states in, their first-fail children
+// and fully fixed states out, in the order of the states.  ctr: [0] children written to
+// `next`, [1] fully fixed states written to `units` (all levels so far), [2] nodes
+// (branching or failed states), [3] failed states, [4] set when a buffer would overflow,
+// [5] the level's first slot in `units`.  off: per state, its children and unit counts,
+// then their exclusive prefix sums (count words).
 struct ExpandArgs {
     const uint32_t *inst;
     const uint32_t *states;
@@ -172,6 +183,7 @@ struct ExpandArgs {
     uint32_t *units;
     int64_t units_cap;
     unsigned long long *ctr;
+    unsigned long long *off;
 };
 
 struct PropArgs {

@@ -21,6 +21,7 @@
 
 namespace cubics {
 
+constexpr int CSP_EINVAL_ = -1;
 constexpr int CSP_ELIMIT_ = -5;
 constexpr int CSP_ETIMEOUT_ = -6;
 constexpr int F_NO_DONATE = 1;
@@ -35,7 +36,8 @@ struct WarpShared {
     long long t_start;
     int64_t sol_off;
     long long wait_ns;    // time spent waiting for a record
-    int32_t maxd, pad;
+    int32_t maxd;
+    int32_t hcnt;         // register kernel: solutions waiting in the hash buffer
     unsigned long long rounds;   // fixpoint rounds
     int32_t pad2[2];
 };
@@ -193,6 +195,11 @@ struct Worker {
     int team;             // batch: index of the team (its queue) being helped
     int inst;             // batch: instance being searched
     int stop;             // a poll saw the stop flag
+    // register kernel: node statistics since they were last added to WarpShared, packed
+    // (nodes bits 0-7, fails 8-15, propagator evaluations 16-31, fixpoint rounds 32-47);
+    // added every 64 nodes at most, so no field overflows (a node evaluates each of its at
+    // most 32 variables once, in at most 32 rounds)
+    unsigned long long cnt;
 
     __device__ __forceinline__ WarpShared &ws() const {
         return *reinterpret_cast<WarpShared *>(&SM[wso]);
@@ -210,6 +217,18 @@ struct Worker {
     }
     // lsm is a power of two
     __device__ __forceinline__ int slot(int k) const { return slots + (k & (lsm - 1)) * R; }
+
+    // add the packed node statistics to WarpShared (whole warp)
+    __device__ __forceinline__ void fold_counts() {
+        if (lane_id() == 0 && cnt) {
+            WarpShared &w = ws();
+            w.nodes += cnt & 0xffull;
+            w.fails += (cnt >> 8) & 0xffull;
+            w.evals += (cnt >> 16) & 0xffffull;
+            w.rounds += cnt >> 32;
+        }
+        cnt = 0;
+    }
 
     // make the shared slot of level k (== top) free
     __device__ void make_room(int k) {
@@ -244,6 +263,7 @@ struct Worker {
     // Node and time limits, every 64 nodes.  In batch mode the node limit is per instance:
     // the team's instance stops (found = 2) and the others go on.
     __device__ __noinline__ void check_limits() {
+        if constexpr (REG) fold_counts();
         refresh_worth();
         if (lane_id() == 0) {
             if (!CUBICS_FINISHED_STATS) {
@@ -331,7 +351,47 @@ struct Worker {
         __syncwarp();
     }
 
-    // record_solution for a node held in registers (lane i: the one value of x_i)
+    // SM offset of the warp's deferred solution-hash buffer (register kernel)
+    __device__ __forceinline__ int hbuf() const {
+        return wso + WS_WORDS + SA.feat_words + SA.list_words;
+    }
+
+    // Hash the solutions waiting in the buffer, one per lane (each lane runs one solution's
+    // chain of n splitmix64 steps, the same chain as record_solution), and add their sum and
+    // xor to WarpShared.  Whole warp.
+    __device__ __noinline__ void hash_flush_reg() {
+        const int lane = lane_id();
+        const int n = I.n;
+        WarpShared &w = ws();
+        const int waiting = w.hcnt;
+        unsigned long long h = 0ull, hx = 0ull;
+        if (lane < waiting) {
+            const uint32_t *row = &SM[hbuf() + lane * HB_STRIDE];
+            h = 0x9E3779B97F4A7C15ull;
+            uint32_t word = 0u;
+            for (int i = 0; i < n; ++i) {
+                if ((i & 3) == 0) word = row[i >> 2];
+                const unsigned vi = (unsigned)(I.lo0 + (int)((word >> ((i & 3) * 8)) & 0xffu));
+                h = splitmix64(h ^ (((unsigned long long)(unsigned)i << 32) | vi));
+            }
+            hx = h;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            h += __shfl_xor_sync(FULLMASK, h, o);
+            hx ^= __shfl_xor_sync(FULLMASK, hx, o);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            w.hsum += h;
+            w.hxor ^= hx;
+            w.hcnt = 0;
+        }
+        __syncwarp();
+    }
+
+    // record_solution for a node held in registers (lane i: the one value of x_i).  The
+    // solution hash is deferred: the values (offsets from lo0, one byte each) go to the
+    // warp's buffer, and every HB_SOLS solutions hash_flush_reg hashes them together.
     __device__ __noinline__ void record_solution_reg(uint32_t d) {
         const int lane = lane_id();
         const int n = I.n;
@@ -343,19 +403,19 @@ struct Worker {
             stop = 1;
         }
         if (!keep) return;
-        const int val = I.lo0 + __ffs(d) - 1;
-        unsigned long long h = 0x9E3779B97F4A7C15ull;
-        for (int i = 0; i < n; ++i) {
-            const unsigned vi = (unsigned)__shfl_sync(FULLMASK, val, i);
-            h = splitmix64(h ^ (((unsigned long long)(unsigned)i << 32) | vi));
-        }
+        const int bit = __ffs(d) - 1;
+        const int val = I.lo0 + bit;
+        WarpShared &w = ws();
+        const int k = w.hcnt;
+        if (lane < n) reinterpret_cast<uint8_t *>(&SM[hbuf() + k * HB_STRIDE])[lane] = (uint8_t)bit;
+        __syncwarp();
         if (lane == 0) {
-            WarpShared &w = ws();
             w.sols++;
-            w.hsum += h;
-            w.hxor ^= h;
+            w.hcnt = k + 1;
             if (SA.batch) atomicAdd(&SA.results[inst].solutions, 1ull);
         }
+        __syncwarp();
+        if (k + 1 == HB_SOLS) hash_flush_reg();
         long long slot_off = -1;
         if (SA.mode == 1) {
             slot_off = ws().sol_off;
@@ -701,15 +761,9 @@ struct Worker {
         if (!failed) failed = fixpoint_reg<ST>(I, d, pending, full ? 0u : done, ev, rnd);
         const bool split_root = full && !SA.batch && SA.nparts > 1;
         const bool counted = !split_root || SA.part == 0;
-        if (lane == 0 && counted) {
-            WarpShared &w = ws();
-            w.nodes++;
-            w.evals += ev;
-            w.rounds += rnd;
-        }
+        if (counted) cnt += 1ull + (failed ? 0x100ull : 0ull) + (ev << 16) + (rnd << 32);
         if (polled) stop = __shfl_sync(FULLMASK, p_stop, 0);
         if (failed) {
-            if (lane == 0 && counted) ws().fails++;
             refill();
             return;
         }
@@ -876,7 +930,14 @@ struct Worker {
                 sleep = sleep < CUBICS_POLL_MAX_NS ? sleep * 2 : CUBICS_POLL_MAX_NS;
             }
             if (lane == 0) ws().wait_ns += global_ns() - t0;
-            if (!got) return;
+            if (!got) {
+                if constexpr (REG) {
+                    // before a batch worker moves to another instance (other n and lo0)
+                    fold_counts();
+                    if (ws().hcnt > 0) hash_flush_reg();
+                }
+                return;
+            }
             taken = tick;
             // the record's size bin (its share of unfixed variables); with running credit,
             // it counts in its bin now and its nodes are credited as they are explored (every
@@ -904,6 +965,7 @@ struct Worker {
             w.nodes = w.fails = w.sols = w.hsum = w.hxor = 0;
             w.evals = w.steals = w.spills = 0;
             w.maxd = 0;
+            w.hcnt = 0;
             w.sol_off = 0;
             w.wait_ns = 0;
             w.rounds = 0;
@@ -913,6 +975,10 @@ struct Worker {
     }
 
     __device__ void flush() {
+        if constexpr (REG) {
+            fold_counts();
+            if (ws().hcnt > 0) hash_flush_reg();
+        }
         if (lane_id() == 0) {
             GState *g = SA.g;
             WarpShared &w = ws();
@@ -945,7 +1011,11 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
     __shared__ int s_inst, s_team;
     if (threadIdx.x == 0) SA = Ap;
     __syncthreads();
-    const int per_warp = SA.lsm * SA.rmax + WS_WORDS + SA.feat_words + SA.list_words;
+    if (REG && SA.hash_words < HB_WORDS) {      // no room for the deferred solution hashes
+        if (threadIdx.x == 0) atomicCAS(&SA.g->status, 0, CSP_EINVAL_);
+        return;
+    }
+    const int per_warp = SA.lsm * SA.rmax + WS_WORDS + SA.feat_words + SA.list_words + SA.hash_words;
     if (EXT && SA.mlp_off >= 0) {    // the brancher's weights, staged once per block
         for (int i = threadIdx.x; i < PK_WORDS; i += blockDim.x) SM[SA.mlp_off + i] = __ldg(SA.mlp + i);
         __syncthreads();
@@ -964,6 +1034,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
     wk.pbin = 0;
     wk.credited = 0;
     wk.stop = 0;
+    wk.cnt = 0;
     wk.team = 0;
     wk.inst = 0;
     wk.init_shared();
@@ -1164,57 +1235,124 @@ __global__ void __launch_bounds__(1024) propagate_block_kernel(PropArgs P) {
     }
 }
 
-// One level of the depth-k split of a single problem, a warp per propagated state: a failed
-// state is a node and a fail; a state with every variable fixed is a unit as it stands (its
-// node is counted when the unit is searched); any other state is a node whose first-fail
-// variable (fewest values, lowest index) gives one child per value, ascending, written to
-// `next` at slots reserved with an atomic add (the children of different states interleave
-// in any order).  A reservation beyond a buffer sets the overflow counter and writes nothing.
+// One level of the depth-k split of a single problem, in three passes over the propagated
+// states (a warp per state in the first and last).  A failed state is a node and a fail; a
+// state with every variable fixed is a unit as it stands (its node is counted when the unit
+// is searched); any other state is a node whose first-fail variable (fewest values, lowest
+// index) gives one child per value, ascending.  Children and units keep the order of their
+// parents (an exclusive scan of the per-state counts places them), so the units of a split
+// come out in the same order at every run: the order of a depth-first search.
+
+// first-fail branching variable of a state and its number of values; y = -1 when every
+// variable is fixed
 template <int W>
-__global__ void __launch_bounds__(256) expand_level_kernel(ExpandArgs E) {
+__device__ __forceinline__ void branch_of(const uint32_t *st, int n, int &y, int &c) {
+    unsigned best = 0xffffffffu;
+    for (int v = lane_id(); v < n; v += 32) {
+        int pc = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) pc += __popc(st[v * W + k]);
+        if (pc > 1) best = min(best, ((unsigned)pc << 16) | (unsigned)v);
+    }
+    best = __reduce_min_sync(FULLMASK, best);
+    y = best == 0xffffffffu ? -1 : (int)(best & 0xffffu);
+    c = best == 0xffffffffu ? 0 : (int)(best >> 16);
+}
+
+// pass 1: off[s] = children of state s (low 32 bits) | 1 << 32 if it is a unit; nodes and
+// fails counted
+template <int W>
+__global__ void __launch_bounds__(256) expand_count_kernel(ExpandArgs E) {
     const int lane = lane_id();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = (int)E.inst[H_N], S = (int)E.inst[H_S];
     for (int s = warp; s < E.count; s += nwarps) {
-        const uint32_t *st = E.states + (size_t)s * S;
         if (E.failed[s]) {
             if (lane == 0) {
                 atomicAdd(&E.ctr[2], 1ull);
                 atomicAdd(&E.ctr[3], 1ull);
+                E.off[s] = 0ull;
             }
             continue;
         }
-        unsigned best = 0xffffffffu;
-        for (int v = lane; v < n; v += 32) {
-            int pc = 0;
-#pragma unroll
-            for (int k = 0; k < W; ++k) pc += __popc(st[v * W + k]);
-            if (pc > 1) best = min(best, ((unsigned)pc << 16) | (unsigned)v);
-        }
-        best = __reduce_min_sync(FULLMASK, best);
-        if (best == 0xffffffffu) {
-            unsigned long long slot = 0;
-            if (lane == 0) slot = atomicAdd(&E.ctr[1], 1ull);
-            slot = __shfl_sync(FULLMASK, slot, 0);
-            if ((long long)slot < E.units_cap) {
-                for (int k = lane; k < S; k += 32) E.units[(size_t)slot * S + k] = st[k];
-            } else if (lane == 0) {
-                atomicExch(&E.ctr[4], 1ull);
-            }
-            continue;
-        }
-        const int y = (int)(best & 0xffffu), c = (int)(best >> 16);
-        unsigned long long base = 0;
+        int y, c;
+        branch_of<W>(E.states + (size_t)s * S, n, y, c);
         if (lane == 0) {
-            atomicAdd(&E.ctr[2], 1ull);
-            base = atomicAdd(&E.ctr[0], (unsigned long long)c);
+            if (y >= 0) atomicAdd(&E.ctr[2], 1ull);
+            E.off[s] = y < 0 ? (1ull << 32) : (unsigned long long)c;
         }
-        base = __shfl_sync(FULLMASK, base, 0);
-        if ((long long)(base + c) > E.next_cap) {
-            if (lane == 0) atomicExch(&E.ctr[4], 1ull);
+    }
+}
+
+// pass 2 (one block of 1024 threads): exclusive scan of off[0 .. count); then the level's
+// children (ctr[0]) and the units so far (ctr[1], the level's first unit slot in ctr[5]), or
+// the overflow flag (ctr[4]) when the children or the units would not fit.  A state has at
+// most 256 children and a level at most 2^31 / 256 states, so the packed halves never carry.
+template <int W>
+__global__ void __launch_bounds__(1024) expand_scan_kernel(ExpandArgs E) {
+    __shared__ unsigned long long wsum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int per = (E.count + 1023) / 1024;
+    const int b = min(E.count, t * per), e = min(E.count, b + per);
+    unsigned long long sum = 0ull;
+    for (int i = b; i < e; ++i) sum += E.off[i];
+    unsigned long long x = sum;                      // inclusive scan within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULLMASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {                                  // inclusive scan of the warp totals
+        unsigned long long w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULLMASK, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long run = x - sum + (wid > 0 ? wsum[wid - 1] : 0ull);
+    for (int i = b; i < e; ++i) {
+        const unsigned long long v = E.off[i];
+        E.off[i] = run;
+        run += v;
+    }
+    if (t == 1023) {
+        const unsigned long long children = wsum[31] & 0xffffffffull, units = wsum[31] >> 32;
+        const unsigned long long u0 = E.ctr[1];
+        if ((long long)children > E.next_cap || (long long)(u0 + units) > E.units_cap) {
+            E.ctr[4] = 1ull;
+        } else {
+            E.ctr[0] = children;
+            E.ctr[1] = u0 + units;
+            E.ctr[5] = u0;
+        }
+    }
+}
+
+// pass 3: every child and unit written at its place (nothing when the level overflowed)
+template <int W>
+__global__ void __launch_bounds__(256) expand_write_kernel(ExpandArgs E) {
+    if (*(volatile unsigned long long *)&E.ctr[4]) return;
+    const int lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int n = (int)E.inst[H_N], S = (int)E.inst[H_S];
+    const unsigned long long u0 = E.ctr[5];
+    for (int s = warp; s < E.count; s += nwarps) {
+        if (E.failed[s]) continue;
+        const uint32_t *st = E.states + (size_t)s * S;
+        int y, c;
+        branch_of<W>(st, n, y, c);
+        const unsigned long long o = E.off[s];
+        if (y < 0) {
+            uint32_t *u = E.units + (size_t)(u0 + (o >> 32)) * S;
+            for (int k = lane; k < S; k += 32) u[k] = st[k];
             continue;
         }
+        const unsigned long long base = o & 0xffffffffull;
         long long j = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -1317,7 +1455,9 @@ cudaError_t launch_prop_t(const PropArgs &P, int blocks, int threads, size_t sme
 #define CUBICS_DEFINE_WIDTH(WW)                                                              \
     CUBICS_DEFINE_SEARCH(WW, false, )                                                        \
     cudaError_t launch_expand_w##WW(const ExpandArgs &E, int blocks, cudaStream_t s) {       \
-        expand_level_kernel<WW><<<blocks, 256, 0, s>>>(E);                                  \
+        expand_count_kernel<WW><<<blocks, 256, 0, s>>>(E);                                  \
+        expand_scan_kernel<WW><<<1, 1024, 0, s>>>(E);                                       \
+        expand_write_kernel<WW><<<blocks, 256, 0, s>>>(E);                                  \
         return cudaGetLastError();                                                          \
     }                                                                                       \
     cudaError_t launch_prop_w##WW(bool st_, const PropArgs &P, int b, int t, size_t sm,     \

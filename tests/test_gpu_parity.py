@@ -445,6 +445,25 @@ def test_split_full_size_against_oracle_reference(N, depth):
     assert rc == 0 and st1["units"] == 1 and st1["nodes"] == st["nodes"]
 
 
+def test_split_level_overflow_keeps_the_last_level_that_fits():
+    """16-queens split at depth 6: a level of more than 2^16 states (the level buffers of a
+    16-variable problem) is not expanded, and the level above it becomes the units; the
+    counts still equal the oracle's full-size run."""
+    from paper_1909_09213_gb300 import shard
+    ref = oracle_reference(16)
+    p = K.Csp(I.queens(16))
+    p.set_tiling(K.tiling(split_depth=6))
+    rc, st, _ = p.solve(K.CSP_ALL, 0)
+    assert rc == 0
+    assert (st["nodes"], st["fails"], st["solutions"], st["sol_hash_sum"], st["sol_hash_xor"]) == (
+        ref["nodes"], ref["fails"], ref["solutions"], ref["hash_sum"], ref["hash_xor"])
+    n, W = p.layout()[:2]
+    root = p.root_domains().ravel()
+    cuts = {d: len(shard.split_units(p.propagate, root, n, W, d)[0]) for d in (4, 5)}
+    assert cuts[4] <= 1 << 16 < cuts[5]              # the level at depth 5 does not fit
+    assert st["units"] == cuts[4]
+
+
 @pytest.mark.parametrize("tname", ["split1", "split3"])
 def test_split_wide_domains_and_every_kind(tname):
     for m in [strided_queens(9, 31), strided_queens(8, 13, alldiff=True, rows=True),
