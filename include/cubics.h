@@ -71,12 +71,20 @@ typedef struct {
                                  with CSP_EINVAL */
     int32_t smem_levels;      /* search-stack levels kept in shared memory per worker */
     int32_t queue_records;    /* capacity of each work queue (power of two) */
-    int32_t threads_per_node; /* 0 or 32: a warp per node (the search kernels' only shape);
-                                 64..1024 (a multiple of 32): csp_propagate gives each domain
-                                 state a whole block, its warps sharing out the constraints of
-                                 each kind (constraint-parallel propagation of one node too
-                                 large for a warp, Section 2.2's grouping by kind); a search
-                                 plan with it is CSP_EINVAL */
+    int32_t threads_per_node; /* 16: two sibling nodes per warp, a half-warp each: search
+                                 of all solutions of a one-word int_ne problem of at most 16
+                                 variables (the register-held kernel, first-fail brancher);
+                                 anything else with 16 is CSP_EINVAL.  The two siblings'
+                                 fixpoints share every instruction; the search visits the
+                                 same nodes (same counts and hashes), child 0's subtree
+                                 first, and max_depth counts stack levels (up to 2n - 1).
+                                 32: a warp per node.  0: the library's choice (16 where it
+                                 applies, else 32).  64..1024 (a multiple of 32):
+                                 csp_propagate gives each domain state a whole block, its
+                                 warps sharing out the constraints of each kind
+                                 (constraint-parallel propagation of one node too large for
+                                 a warp, Section 2.2's grouping by kind); a search plan with
+                                 it is CSP_EINVAL */
     int32_t split_depth;      /* all-solution search of one problem (csp_solve / csp_launch):
                                  k = 1..8: the first k levels are expanded on the device (one
                                  fixpoint and one expansion kernel per level; csp_launch then

@@ -135,6 +135,22 @@ int make_shape(const csp_tiling &t, int W, int R, int depth, int cons, bool batc
 // 10^7 nodes, the same for 2 * 10^8); -1 keeps one queue shared by every worker.
 int split_depth_of(const csp_tiling &t) { return t.split_depth == 0 ? 3 : t.split_depth; }
 
+// Two sibling nodes per warp, a half-warp each (threads_per_node 16, or 0: the library's
+// choice): the register kernel (one-word int_ne, no learned brancher or logging) on problems
+// of at most 16 variables, all-solution search.  1: pairs; 0: a warp per node; CSP_EINVAL:
+// 16 asked where pairs do not apply.
+int pairs_of(const csp_tiling &t, bool reg_kernel, int nmax, bool all) {
+    const bool ok = reg_kernel && nmax <= 16 && all;
+    if (t.threads_per_node == 16) return ok ? 1 : CSP_EINVAL;
+    return (t.threads_per_node == 0 && ok) ? 1 : 0;
+}
+
+// Search levels a worker's stack holds.  Levels are nodes with an unfixed variable, so their
+// tree depths are 0 .. n - 1 and rise from the bottom of the stack to the top: one per depth
+// (n + 1 with a margin), or with pairs two per depth but the root's (a sibling's level
+// waits below the level being searched), 2n - 1 (2n planned).
+int stack_depth(int n, bool pairs) { return pairs ? 2 * n : n + 1; }
+
 // carve consecutive 256-byte aligned regions
 struct Carver {
     size_t off = 0;
@@ -155,6 +171,7 @@ struct Carver {
 struct Plan {
     Shape shape;
     int R = 0, depth = 0;
+    int pairs = 0;                   // two sibling nodes per warp (register kernel)
     size_t o_inst = 0, o_off = 0, o_g = 0, o_team = 0, o_qseq = 0, o_qrec = 0, o_spill = 0,
            o_sols = 0, o_mlp_params = 0, o_mlp_packed = 0;
     // all-solution search split at depth k into units solved by per-block teams
@@ -448,8 +465,11 @@ int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<ui
         return CSP_OK;
     }
     const int R = record_words(h->n * h->W, h->W);
-    const int depth = h->n + 1;
     const bool learned = h->brancher == CSP_BR_LEARNED;
+    const int pairs = pairs_of(h->tiling, (B[H_FLAGS] & FLAG_NE_REG) != 0 && !learned, h->n,
+                               mode == CSP_ALL);
+    if (pairs < 0) return pairs;
+    const int depth = stack_depth(h->n, pairs > 0);
     // the device expansion of the first levels branches first-fail: a learned ordering
     // searches the whole tree with one shared queue
     p.split = allow_split && mode == CSP_ALL && split_depth_of(h->tiling) > 0 && h->nparts == 1 &&
@@ -460,6 +480,7 @@ int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<ui
     const Shape &s = p.shape;
     p.R = R;
     p.depth = depth;
+    p.pairs = pairs;
     if (p.split) {
         // per-block teams (one queue each) over the units, the level buffers and the units
         const size_t S4 = (size_t)h->n * h->W * 4;
@@ -527,6 +548,7 @@ SearchArgs single_args(const csp *h, const Plan &P, uint8_t *w, int32_t mode, in
     A.lsm = P.shape.lsm;
     A.rmax = P.R;
     A.depth = P.depth;
+    A.pairs = P.pairs;
     A.stage_words = P.shape.stage_words;
     A.qmask = P.shape.qcap - 1;
     A.flags = lim ? lim->flags : 0;
@@ -746,8 +768,8 @@ int csp_layout(const csp_t *h, int32_t *n, int32_t *W, int32_t *lo0) {
 // queue capacity a power of two; threads per node 0 or a multiple of 32 up to 1024
 static bool tiling_ok(const csp_tiling &t) {
     const int tp = t.threads_per_node;
-    return !(t.queue_records & (t.queue_records - 1)) && tp >= 0 && tp <= 1024 && tp % 32 == 0 &&
-           t.split_depth >= -1 && t.split_depth <= 8;
+    return !(t.queue_records & (t.queue_records - 1)) && tp >= 0 && tp <= 1024 &&
+           (tp % 32 == 0 || tp == 16) && t.split_depth >= -1 && t.split_depth <= 8;
 }
 
 int csp_set_tiling(csp_t *h, const csp_tiling *t) {
@@ -1027,6 +1049,7 @@ int csp_solve(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out, const csp_l
 int csp_propagate(csp_t *h, int32_t count, const uint32_t *dom_in, uint32_t *dom_out,
                   int32_t *failed) {
     if (!h || count < 0 || (count > 0 && (!dom_in || !dom_out || !failed))) return CSP_EINVAL;
+    if (h->tiling.threads_per_node == 16) return CSP_EINVAL;     // two nodes per warp: search only
     if (!h->ws) return CSP_ESTATE;
     if (count == 0) return CSP_OK;
     Plan L;
@@ -1114,6 +1137,8 @@ void csp_destroy(csp_t *h) {
 struct BatchPlan {
     Shape shape;
     int R = 4;
+    int depth = 2;                   // stack levels per worker
+    int pairs = 0;                   // pairs possible (used in all-solution launches)
     size_t o_arena = 0, o_ioff = 0, o_soff = 0, o_g = 0, o_teams = 0, o_qseq = 0, o_qrec = 0,
            o_spill = 0, o_sols = 0, o_res = 0, o_mlp_params = 0, o_mlp_packed = 0;
     size_t bytes = 0;
@@ -1156,7 +1181,12 @@ int plan_batch(const csp_batch *b, BatchPlan *P) {
     BatchPlan p;
     const bool learned = b->brancher == CSP_BR_LEARNED;
     p.R = record_words(b->nmax * b->W, b->W, b->logbuf ? LOG_EXTRA : 0);
-    int rc = make_shape(b->tiling, b->W, p.R, b->depth, b->cons_max, true, learned,
+    // the plan does not know the mode: room for pairs wherever an all-solution launch may use them
+    const int pairs = pairs_of(b->tiling, b->all_reg && !learned && !b->logbuf, b->nmax, true);
+    if (pairs < 0) return pairs;
+    p.pairs = pairs;
+    p.depth = stack_depth(b->nmax, pairs > 0);
+    int rc = make_shape(b->tiling, b->W, p.R, p.depth, b->cons_max, true, learned,
                         b->logbuf != nullptr, b->nmax, b->ntab_max, b->all_reg, &p.shape);
     if (rc) return rc;
     const Shape &s = p.shape;
@@ -1169,7 +1199,7 @@ int plan_batch(const csp_batch *b, BatchPlan *P) {
     p.o_teams = c.take((size_t)s.blocks * sizeof(Team));
     p.o_qseq = c.take((size_t)s.blocks * s.qcap * 4);
     p.o_qrec = c.take((size_t)s.blocks * s.qcap * p.R * 4);
-    p.o_spill = c.take((size_t)s.blocks * s.warps * b->depth * p.R * 4);
+    p.o_spill = c.take((size_t)s.blocks * s.warps * p.depth * p.R * 4);
     p.o_sols = c.take((size_t)std::max<int64_t>(b->sol_words, 1) * 4);
     p.o_res = c.take(count * sizeof(InstResult));
     p.o_mlp_params = c.take(learned ? CSP_MLP_PARAMS * 2 : 0);
@@ -1190,7 +1220,8 @@ SearchArgs batch_args(csp_batch *b, const csp_limits *lim) {
     A.batch = 1;
     A.lsm = b->plan.shape.lsm;
     A.rmax = b->plan.R;
-    A.depth = b->depth;
+    A.depth = b->plan.depth;
+    A.pairs = b->plan.pairs && b->mode == CSP_ALL;
     A.stage_words = b->plan.shape.stage_words;
     A.qmask = b->plan.shape.qcap - 1;
     A.flags = lim ? lim->flags : 0;
@@ -1390,6 +1421,7 @@ static int batch_upload(csp_batch *b, int32_t mode) {
 
 int csp_batch_launch(csp_batch_t *b, const csp_limits *lim, int32_t use_graph) {
     if (!b || !b->uploaded) return CSP_ESTATE;
+    if (b->tiling.threads_per_node == 16 && b->mode != CSP_ALL) return CSP_EINVAL;
     const csp_limits L = lim ? *lim : csp_limits{0, 0, 0, 0, 0};
     SearchArgs A = batch_args(b, &L);
     cudaError_t e = cudaSuccess;

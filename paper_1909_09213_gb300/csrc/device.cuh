@@ -521,6 +521,64 @@ __device__ __forceinline__ bool fixpoint_reg(const IV<ST> &I, uint32_t &d, uint3
     return false;
 }
 
+// Fixpoints of two nodes at once, one per half-warp (n <= 16): lane 16h + i holds D(x_i) of
+// node h.  The same rounds as fixpoint_reg for each half, in the same instructions: bits
+// 16h + v of `pending` and `done` are node h's sets (a ballot yields both halves' sets in
+// one word), a lane shuffles from its own half and loads the offset mask of its half's
+// variable.  A half whose node failed stops at the round that emptied a domain, as
+// fixpoint_reg returns there.  Returns the failed halves (0x0000ffff: node 0, 0xffff0000:
+// node 1); evals and rounds of node h in bits 16h .. 16h + 15 of ev and rnd.
+template <bool ST>
+__device__ __forceinline__ uint32_t fixpoint_pair_reg(const IV<ST> &I, uint32_t &d,
+                                                      uint32_t pending, uint32_t done,
+                                                      uint32_t &ev, uint32_t &rnd) {
+    const int lane = lane_id();
+    const int i = lane & 15;
+    const uint32_t half = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
+    const bool act = i < I.n;
+    const int nm = (int)I.w(H_OFF_NEMASK);
+    uint32_t failed = 0u;
+    while (pending) {
+        const uint32_t p0 = pending & 0xffffu, p1 = pending >> 16;
+        ev += (uint32_t)__popc(p0) | ((uint32_t)__popc(p1) << 16);
+        rnd += (p0 ? 1u : 0u) | (p1 ? 0x10000u : 0u);
+        const int a = __ffs(d) - 1;               // the value of each fixed variable
+        uint32_t rm = 0u;
+        uint32_t p = pending & half;              // this lane's node (bit 16h + v)
+        // two fixed variables of each node per step; a node with none left takes a masked step
+        while (__any_sync(FULLMASK, p != 0u)) {
+            const bool h0 = p != 0u;
+            const int v0 = h0 ? __ffs(p) - 1 : 0;
+            p &= p - 1u;
+            const bool h1 = p != 0u;
+            const int v1 = h1 ? __ffs(p) - 1 : v0;
+            p &= p - 1u;
+            const int a0 = __shfl_sync(FULLMASK, a, v0);
+            const int a1 = __shfl_sync(FULLMASK, a, v1);
+            const uint2 m0 = ne_mask(I, nm, v0 & 15, i);
+            const uint2 m1 = ne_mask(I, nm, v1 & 15, i);
+            rm |= (h0 ? ne_removed(m0, a0) : 0u) | (h1 ? ne_removed(m1, a1) : 0u);
+        }
+        d &= ~rm;
+        done |= pending;
+        const uint32_t empty = __ballot_sync(FULLMASK, act && d == 0u);
+        failed |= ((empty & 0xffffu) ? 0xffffu : 0u) | ((empty >> 16) ? 0xffff0000u : 0u);
+        pending = __ballot_sync(FULLMASK, act && (d & (d - 1u)) == 0u) & ~done & ~failed;
+    }
+    return failed;
+}
+
+// first-fail within each half-warp (n <= 16): the unfixed variable of the lane's node with the
+// fewest values, lowest index on ties; -1 when every variable is fixed or `skip`
+__device__ __forceinline__ int select_first_fail_pair(uint32_t d, int n, bool skip) {
+    const int i = lane_id() & 15;
+    uint32_t key = (!skip && i < n && (d & (d - 1u))) ? ((uint32_t)__popc(d) << 5) | (uint32_t)i
+                                                       : 0xffffffffu;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(FULLMASK, key, o));
+    return key == 0xffffffffu ? -1 : (int)(key & 31u);
+}
+
 // first-fail over register-held domains: the unfixed variable with the fewest values, lowest
 // index on ties; -1 when every variable is fixed
 __device__ __forceinline__ int select_first_fail_reg(uint32_t d, int n) {

@@ -164,6 +164,9 @@ struct SearchArgs {
                               // the launch (the instances are parts of one search)
     int32_t hash_words;       // per-warp words of the deferred solution-hash buffer (register
                               // kernel: HB_SOLS solutions of HB_STRIDE words), else 0
+    int32_t pairs;            // register kernel, all solutions, n <= 16: two sibling nodes per
+                              // warp (the stack has room for 2n levels)
+    int32_t pad_args;
 };
 
 // One level of the depth-k split of a single problem (expand_count_kernel,

@@ -164,6 +164,10 @@ static __device__ bool q_take(uint32_t *seq, uint32_t *rec, uint32_t t, int dst,
 #endif
 
 // most records one donation check may push
+// the paired expansion (two sibling nodes per warp) inline in the search loop, or a call
+#ifndef CUBICS_PAIR_INLINE
+#define CUBICS_PAIR_INLINE __forceinline__
+#endif
 #ifndef CUBICS_DONATE_MAX
 #define CUBICS_DONATE_MAX 16
 #endif
@@ -263,7 +267,13 @@ struct Worker {
     // Node and time limits, every 64 nodes.  In batch mode the node limit is per instance:
     // the team's instance stops (found = 2) and the others go on.
     __device__ __noinline__ void check_limits() {
-        if constexpr (REG) fold_counts();
+        // nodes since the last check: 64 ticks, or the register kernel's own count (a tick
+        // of a pair is two nodes)
+        unsigned long long nn = 64ull;
+        if constexpr (REG) {
+            nn = cnt & 0xffull;
+            fold_counts();
+        }
         refresh_worth();
         if (lane_id() == 0) {
             if (!CUBICS_FINISHED_STATS) {
@@ -271,10 +281,10 @@ struct Worker {
                 credited = tick;
             }
             if (SA.node_limit > 0 && SA.batch && !SA.global_limits) {
-                const unsigned long long tot = atomicAdd(&T->progress, 64ull) + 64ull;
+                const unsigned long long tot = atomicAdd(&T->progress, nn) + nn;
                 if ((long long)tot >= SA.node_limit) atomicCAS(&T->found, 0, 2);
             } else if (SA.node_limit > 0) {
-                const unsigned long long tot = atomicAdd(&SA.g->node_progress, 64ull) + 64ull;
+                const unsigned long long tot = atomicAdd(&SA.g->node_progress, nn) + nn;
                 if ((long long)tot >= SA.node_limit) {
                     atomicCAS(&SA.g->status, 0, CSP_ELIMIT_);
                     atomicExch(&SA.g->abort, 1);
@@ -801,6 +811,125 @@ struct Worker {
         }
     }
 
+    // Solutions of a pair of nodes (expand_pair_reg): bit h of `sol` for node h, whose lanes
+    // 16h + i hold the one value of x_i.  The values go to the hash buffer (node 0 first) and,
+    // with a cap, to the solution store.
+    __device__ __noinline__ void record_solution_pair(uint32_t d, uint32_t sol) {
+        const int lane = lane_id();
+        const int h = lane >> 4, i = lane & 15;
+        const int n = I.n;
+        const int ns = __popc(sol);
+        WarpShared &w = ws();
+        if (w.hcnt + ns > HB_SOLS) hash_flush_reg();
+        const int k = w.hcnt;
+        const bool mine = (sol >> h) & 1u;
+        const int bit = __ffs(d) - 1;
+        const int at = k + ((h == 1 && (sol & 1u)) ? 1 : 0);
+        if (mine && i < n) reinterpret_cast<uint8_t *>(&SM[hbuf() + at * HB_STRIDE])[i] = (uint8_t)bit;
+        __syncwarp();
+        if (lane == 0) {
+            w.sols += (unsigned long long)ns;
+            w.hcnt = k + ns;
+            if (SA.batch) atomicAdd(&SA.results[inst].solutions, (unsigned long long)ns);
+        }
+        __syncwarp();
+        if (k + ns == HB_SOLS) hash_flush_reg();
+        if (SA.cap > 0 && SA.sols != nullptr) {
+            for (int s2 = 0; s2 < 2; ++s2) {
+                if (!((sol >> s2) & 1u)) continue;
+                unsigned long long t = 0;
+                if (lane == 0 && ld_volatile((const uint32_t *)&SA.g->stored) < (uint32_t)SA.cap)
+                    t = atomicAdd(&SA.g->stored, 1ull) + 1ull;
+                t = __shfl_sync(FULLMASK, t, 0);
+                if (t > 0 && (long long)t <= SA.cap && h == s2 && i < n)
+                    SA.sols[(long long)(t - 1) * n + i] = I.lo0 + bit;
+            }
+            __syncwarp();
+        }
+    }
+
+    // expand_reg for two children at once (all-solution search, n <= 16): the two lowest
+    // untried values of the top level, child h in half-warp h (lane 16h + i: D(x_i)).  Each
+    // child fails, is a solution or opens a level; child 1's level goes below child 0's, so
+    // child 0's subtree is searched first, and every node is still visited once: the counts
+    // and hashes are those of the depth-first search.  The stack holds up to two levels per
+    // depth (2n - 1 in all; the plan gives it 2n).
+    __device__ CUBICS_PAIR_INLINE void expand_pair_reg(int P, int p, uint32_t r) {
+        const int lane = lane_id();
+        const int h = lane >> 4, i = lane & 15;
+        const int n = I.n;
+        const int v0 = __ffs(r) - 1;
+        const uint32_t r1 = r & (r - 1u);
+        const int v1 = __ffs(r1) - 1;
+        const uint32_t rest = r1 & (r1 - 1u);
+        const int x = (int)SM[P + S + 1];
+        const bool act = i < n;
+        uint32_t d = act ? SM[P + i] : 0u;
+        // the parent is at its fixpoint: its fixed variables' consequences are in d already
+        const uint32_t done = __ballot_sync(FULLMASK, act && (d & (d - 1u)) == 0u);
+        if (i == x) d = 1u << (h ? v1 : v0);
+        __syncwarp();
+        int cl;
+        if (rest == 0u) {                 // the last two values: the level's slot is reused
+            cl = p;
+            top = p;
+        } else {
+            if (lane == 0) SM[P + S] = rest;
+            cl = p + 1;
+            make_room(cl);
+        }
+        __syncwarp();
+        tick++;
+        const bool polled = (tick & (CUBICS_POLL_EVERY - 1u)) == 0u;
+        const int p_stop = polled ? poll() : 0;
+        uint32_t p_head = 0, p_prom = 0;
+        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? (SA.batch ? 0u : CUBICS_HUNGRY_EVERY - 1u) : 7u)) == 0u) &&
+                                tick - taken >= CUBICS_DONATE_AFTER;
+        if (may_donate && lane == 0) {
+            p_head = ld_volatile(&T->head);
+            p_prom = ld_volatile(&T->promised);
+        }
+        if ((tick & 63) == 0) check_limits();
+        uint32_t ev = 0u, rnd = 0u;
+        const uint32_t fm = fixpoint_pair_reg<ST>(I, d, (1u << x) | (1u << (16 + x)), done, ev, rnd);
+        const uint32_t f = (fm & 1u) | ((fm >> 15) & 2u);          // bit h: node h failed
+        cnt += 2ull + ((unsigned long long)__popc(f) << 8) +
+               ((unsigned long long)((ev & 0xffffu) + (ev >> 16)) << 16) +
+               ((unsigned long long)((rnd & 0xffffu) + (rnd >> 16)) << 32);
+        if (polled) stop = __shfl_sync(FULLMASK, p_stop, 0);
+        const int y = select_first_fail_pair(d, n, (f >> h) & 1u);
+        const uint32_t yb = __ballot_sync(FULLMASK, i == 0 && y >= 0);
+        const uint32_t open = (yb & 1u) | ((yb >> 15) & 2u);       // bit h: node h branches
+        const uint32_t sol = ~f & ~open & 3u;
+        if (sol) record_solution_pair(d, sol);
+        if (open) {
+            // node 1's level first (at cl, which has room), node 0's above it
+            const int l0 = (open & 2u) ? cl + 1 : cl;
+            if (open == 3u) make_room(l0);
+            const int C = slot(h ? cl : l0);
+            const uint32_t rw = __shfl_sync(FULLMASK, d, (lane & 16) + (y < 0 ? 0 : y));
+            if ((open >> h) & 1u) {
+                if (act) SM[C + i] = d;
+                if (i == 0) {
+                    SM[C + S] = rw;
+                    SM[C + S + 1] = (uint32_t)y;
+                }
+            }
+            __syncwarp();
+            top = cl + __popc(open);
+            if (lane == 0 && top > ws().maxd) ws().maxd = top;
+        } else {
+            refill();
+        }
+        if (may_donate) {
+            const int owed = max((int)(p_head - p_prom), 0);
+            owed_seen = __shfl_sync(FULLMASK, owed, 0);
+            const int want = min(owed_seen, CUBICS_DONATE_MAX);
+            hungry = want > 0;
+            if (want > 0) donate(want);
+        }
+    }
+
     // expand() for register-held nodes: the parent's domains go straight into registers; only
     // a child that opens a level is written back
     __device__ void expand_reg() {
@@ -811,6 +940,10 @@ struct Worker {
         if (!r) {
             top = p;
             refill();
+            return;
+        }
+        if (SA.pairs && I.n <= 16 && (r & (r - 1u))) {
+            expand_pair_reg(P, p, r);
             return;
         }
         const int v = __ffs(r) - 1;

@@ -83,6 +83,43 @@ def test_workspace_size_grows_with_cap():
     assert p.workspace_bytes(K.CSP_PROPAGATE, 10) > 0
 
 
+def test_two_nodes_per_warp_planning():
+    """threads_per_node = 16 (two sibling nodes per warp) is planned only for all-solution
+    search of one-word int_ne problems of at most 16 variables with the first-fail brancher,
+    with a stack of 2n levels instead of n + 1; 0 picks it there, 32 never."""
+    R = 20                                       # record words of a 16-variable one-word problem
+    p = K.Csp(I.queens(16))
+    size = {}
+    for tpn in (0, 16, 32):
+        p.set_tiling(K.tiling(blocks=2, warps_per_block=4, threads_per_node=tpn, split_depth=-1))
+        size[tpn] = p.workspace_bytes(K.CSP_ALL, 0)
+    assert size[0] == size[16]
+    assert abs(size[16] - size[32] - 2 * 4 * (32 - 17) * R * 4) <= 256
+    p.set_tiling(K.tiling(blocks=2, threads_per_node=16))
+    p.workspace_bytes(K.CSP_ALL, 0)              # split plan too
+    with pytest.raises(K.CspError) as e:
+        p.workspace_bytes(K.CSP_FIRST, 1)
+    assert e.value.code == K.CSP_EINVAL
+    L = K.lib()
+    one = np.zeros(16, np.uint32)
+    failed = np.zeros(1, np.int32)
+    assert L.csp_propagate(p.h, 1, one.ctypes.data_as(K._U32P), one.ctypes.data_as(K._U32P),
+                           failed.ctypes.data_as(K._I32P)) == K.CSP_EINVAL
+    q = K.Csp(I.queens(17))
+    q.set_tiling(K.tiling(blocks=2, threads_per_node=16))
+    with pytest.raises(K.CspError) as e:
+        q.workspace_bytes(K.CSP_ALL, 0)
+    assert e.value.code == K.CSP_EINVAL
+    q.set_tiling(K.tiling(blocks=2, threads_per_node=0))    # the library's choice: a warp
+    q.workspace_bytes(K.CSP_ALL, 0)
+    p.set_brancher(K.CSP_BR_LEARNED, np.zeros(K.MLP_PARAMS, np.uint16))
+    with pytest.raises(K.CspError) as e:
+        p.workspace_bytes(K.CSP_ALL, 0)
+    assert e.value.code == K.CSP_EINVAL
+    with pytest.raises(K.CspError):
+        p.set_tiling(K.tiling(threads_per_node=8))
+
+
 def test_models_build_through_the_abi():
     for m in [I.queens(8), I.worked_example("lin", "table"), I.model_rb(1, 20, 8),
               I.lin_alldiff(3), I.random_tiny(5)]:

@@ -179,6 +179,9 @@ TILINGS = {
     "split1": K.tiling(split_depth=1),
     "split3": K.tiling(split_depth=3, warps_per_block=4),
     "split8": K.tiling(split_depth=8, blocks=5, warps_per_block=2, smem_levels=2),
+    # a warp per node also where two sibling nodes per warp would apply (the default there)
+    "warp": K.tiling(threads_per_node=32, split_depth=-1),
+    "warp-split": K.tiling(threads_per_node=32, warps_per_block=4),
 }
 
 
@@ -280,6 +283,63 @@ def random_ne_model(seed, n, dmax, m):
             y = int(s.int(0, n - 1))
             M.ne.append((x, y, int(s.int(-40, 40)) if k < 6 else int(s.int(-6, 6))))
     return M
+
+
+PAIR_TILINGS = {
+    "pairs": K.tiling(threads_per_node=16),
+    "pairs-shared": K.tiling(threads_per_node=16, split_depth=-1),
+    "pairs-one-worker": K.tiling(threads_per_node=16, blocks=1, warps_per_block=1, split_depth=-1),
+    # two shared-memory levels: pairs push two levels at once through the spill path
+    "pairs-spilling": K.tiling(threads_per_node=16, blocks=3, warps_per_block=4, smem_levels=2,
+                               queue_records=8, split_depth=-1),
+    "pairs-split8": K.tiling(threads_per_node=16, split_depth=8, blocks=5, warps_per_block=2,
+                             smem_levels=2),
+}
+
+
+@pytest.mark.parametrize("tname", list(PAIR_TILINGS))
+def test_two_nodes_per_warp(tname):
+    """Two sibling nodes per warp (a half-warp each) on one-word int_ne models of at most 16
+    variables: nodes, fails, solutions, both hashes and the stored solutions equal the
+    oracle's depth-first search, in every tiling; the stack never needs more than 2n - 1
+    levels."""
+    t = PAIR_TILINGS[tname]
+    for N in range(1, 13):
+        st = search_parity(I.queens(N), t)
+        assert st["solutions"] == queens_count(N)
+        assert st["max_depth"] <= max(1, 2 * N - 1)
+    compared = 0
+    for seed in range(30):
+        n = 6 + seed % 11                                   # 6 .. 16 variables
+        M = random_ne_model(9100 + seed, n, 8 if n < 10 else 6, 2 * n + 6)
+        r = O.solve(O.OracleModel(M), cap=0, variant=1, node_limit=100_000)
+        if r.status < 0:
+            continue
+        search_parity(M, t, cap=3000)
+        compared += 1
+    assert compared >= 15
+
+
+def test_two_nodes_per_warp_limits_and_modes():
+    p = K.Csp(I.queens(12))
+    p.set_tiling(K.tiling(threads_per_node=16, blocks=2, warps_per_block=2, split_depth=-1))
+    rc, st, _ = p.solve(K.CSP_ALL, 0, K.limits(node_limit=5_000))
+    assert rc == K.CSP_ELIMIT and st["nodes"] >= 5_000
+    with pytest.raises(K.CspError) as e:             # pairs are for all-solution search only
+        p.solve(K.CSP_FIRST)
+    assert e.value.code == K.CSP_EINVAL
+    # a batch of such problems: pairs in its all-solution launches, a warp per node otherwise
+    models = [I.queens(N) for N in (6, 8, 9, 10)] + [random_ne_model(9300 + k, 12, 6, 30)
+                                                    for k in range(4)]
+    b = K.Batch([K.Csp(m) for m in models])
+    rc, res = b.solve(K.CSP_ALL)
+    for m, r in zip(models, res):
+        o = O.solve(O.OracleModel(m), cap=0, variant=1)
+        assert (r["nodes"], r["fails"], r["solutions"]) == (o.nodes, o.fails, o.solutions), m.name
+    rc, res = b.solve(K.CSP_FIRST)
+    for m, r in zip(models, res):
+        o = O.solve(O.OracleModel(m), mode=1, cap=1, variant=1)
+        assert r["status"] == o.status, m.name
 
 
 @pytest.mark.parametrize("n,dmax,m", [(6, 8, 12), (12, 6, 30), (20, 5, 70), (32, 3, 110), (33, 3, 110)])
