@@ -80,7 +80,7 @@ struct Team {                 // one work-sharing group (whole grid or one block
     int32_t work;             // records queued or being explored
     int32_t found;            // 1: CSP_FIRST solution recorded; 2: the instance hit its node limit
     int32_t inst;             // instance index (batch mode)
-    int32_t pad0;
+    int32_t helpers;          // batch mode: blocks of other teams that joined (or are joining)
     unsigned long long progress;  // batch mode: nodes spent on the instance (limit accounting)
     int32_t pad1[26];
     uint32_t head;            // consumer tickets (own 128-byte line)

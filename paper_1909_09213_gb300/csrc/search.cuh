@@ -1203,10 +1203,18 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
                     const int c = (blockIdx.x + k) % gridDim.x;
                     Team *Tc = SA.teams + c;
                     if (ld_volatile(&Tc->work) > 0) {
+                        // counted among the team's helpers before the instance is read: the
+                        // owner does not reuse the queue for its next instance while helpers
+                        // may hold tickets of this one
+                        atomicAdd(&Tc->helpers, 1);
                         __threadfence();
-                        t = ld_volatile(&Tc->inst);
-                        team = c;
-                        break;
+                        if (ld_volatile(&Tc->work) > 0) {
+                            __threadfence();
+                            t = ld_volatile(&Tc->inst);
+                            team = c;
+                            break;
+                        }
+                        atomicSub(&Tc->helpers, 1);
                     }
                 }
             }
@@ -1237,8 +1245,22 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
             for (int k = lane; k < wk.R; k += 32)
                 SM[wk.slots + k] = k < wk.S ? root[k] : (k == wk.S + W ? 0xffffffffu : 0u);
             if (lane == 0) {
-                // the block's workers abandoned their tickets when the previous instance
-                // ended; no other block uses this queue before work is set
+                // The block's workers abandoned their tickets when the previous instance
+                // ended, and so do the helpers of other blocks, which leave once they see
+                // work == 0.  Ticket numbers restart at the tail: the queue is reused only
+                // when no helper is left (a stale ticket equal to a new one would take the
+                // new root too).  Bounded wait: past the wait limit the launch stops with
+                // CSP_ETIMEOUT.
+                const long long w0 = global_ns();
+                for (int it = 0; ld_volatile(&T->helpers) > 0; ++it) {
+                    if (it >= (1 << 24) || global_ns() - w0 > SA.wait_limit_ns) {
+                        atomicCAS(&SA.g->status, 0, CSP_ETIMEOUT_);
+                        atomicExch(&SA.g->abort, 1);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
                 const uint32_t t = ld_volatile(&T->tail);
                 T->head = t;
                 T->promised = t + 1u;                       // the root record, pushed below
@@ -1265,6 +1287,10 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
             atomicAdd(&SA.results[i].fails, wk.ws().fails - f0);
         }
         __syncthreads();
+        if (!own && threadIdx.x == 0) {          // every warp of this helper block has left
+            __threadfence();
+            atomicSub(&T->helpers, 1);
+        }
         if (own && threadIdx.x == 0) {
             // every record of the instance is finished (work == 0): its verdict is final
             InstResult &r = SA.results[i];

@@ -505,6 +505,34 @@ def test_split_full_size_against_oracle_reference(N, depth):
     assert rc == 0 and st1["units"] == 1 and st1["nodes"] == st["nodes"]
 
 
+def test_tiny_units_with_many_helper_blocks_repeated():
+    """Small trees split into a few tiny units, most blocks helping other blocks' teams: the
+    owner of a team reuses its queue for its next unit only once no helper is left, so no
+    record is taken twice.  Repeated solves (the interleavings vary), and a batch of many
+    tiny instances, per instance."""
+    for N in (6, 7, 8, 9):
+        r = O.solve(O.OracleModel(I.queens(N)), cap=0, variant=1)
+        p = K.Csp(I.queens(N))
+        p.bind(K.CSP_ALL, 0)
+        p.upload(K.CSP_ALL, 0)
+        for _ in range(40):
+            p.launch()
+            assert p.collect(None) == 0
+            st = p.stats()
+            assert (st["nodes"], st["fails"], st["solutions"], st["sol_hash_sum"],
+                    st["sol_hash_xor"]) == (r.nodes, r.fails, r.solutions, r.hash_sum,
+                                            r.hash_xor), N
+    models = [I.queens(4 + k % 5) for k in range(96)]
+    refs = {m.n: O.solve(O.OracleModel(m), cap=0, variant=1) for m in models}
+    b = K.Batch([K.Csp(m) for m in models])
+    for _ in range(10):
+        rc, res = b.solve(K.CSP_ALL)
+        assert rc == 0
+        for m, x in zip(models, res):
+            o = refs[m.n]
+            assert (x["nodes"], x["fails"], x["solutions"]) == (o.nodes, o.fails, o.solutions), m.name
+
+
 def test_split_level_overflow_keeps_the_last_level_that_fits():
     """16-queens split at depth 6: a level of more than 2^16 states (the level buffers of a
     16-variable problem) is not expanded, and the level above it becomes the units; the
