@@ -307,9 +307,9 @@ class Queens:
         self.p.launch()
 
     def launches_per_step(self):
-        """set-up and search kernels (a split search adds a fixpoint and an expansion kernel
-        per level and starts the batch's queues with its own set-up kernel)"""
-        return 2 + 2 * 3
+        """the split search of the first 3 levels (per level: the fixpoint, then the counting,
+        scan and writing passes of the expansion), the queues' set-up kernel and the search"""
+        return 2 + 4 * 3
 
     def collect(self, K):
         rc = self.p.collect()

@@ -302,9 +302,10 @@ __device__ bool revise_alldiff(const IV<ST> &I, int dom, int chg, int g) {
 // of the domain); more members than values fails.  Every Hall interval equals the interval
 // from the least min to the greatest max of its members, so the candidates are the pairs
 // (a member's min, a member's max).  Lane j holds member j (k <= ADB_MAX = 32); passes over
-// the candidates repeat until one changes nothing.  Returns true on failure.
+// the candidates repeat until one changes nothing.  Returns true on failure.  Out of line: only
+// problems that post such groups run it, and inline its registers made every fixpoint spill.
 template <int W, bool ST>
-__device__ bool revise_alldiff_bc(const IV<ST> &I, int dom, int chg, int g) {
+__device__ __noinline__ bool revise_alldiff_bc(const IV<ST> &I, int dom, int chg, int g) {
     const int lane = lane_id();
     const int grp = (int)I.w(H_OFF_ADB_ROW) + 2 * g;
     const int m0 = (int)I.w(grp), k = (int)I.w(grp + 1);
