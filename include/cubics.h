@@ -336,6 +336,9 @@ int csp_mlp_adam(float *master_dev, float *m_dev, float *v_dev, const float *gra
  * stream capture.  Every call on a device shares the one array and leaves its contents
  * behind; the counters that must start at zero are cleared by each call.  Calls that
  * overlap on the GPU (other host threads, other streams) race on the array: serialise them.
+ * The call waits for the device and copies from pageable host memory, which a stream
+ * capture does not allow: on a capturing stream it returns CSP_ESTATE at once, doing nothing
+ * (the capture stays valid).
  * Returns CSP_ENOMEM when the problem, the launch shape (csp_set_tiling) and cap need more
  * than the array holds, plus the error codes of csp_solve. */
 #define CSP_NOALLOC_SCRATCH_BYTES (16u << 20)

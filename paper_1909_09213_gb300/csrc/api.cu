@@ -1553,6 +1553,17 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
                       const csp_limits *lim, void *cuda_stream) {
     if (!h || mode < 0 || mode > 1 || cap < 0 || cap > INT32_MAX) return CSP_EINVAL;
     if (cap > 0 && !sol_out) return CSP_EINVAL;
+    // The call waits for the device and copies from pageable host memory, neither of which
+    // may happen on a capturing stream (it would invalidate the caller's capture): refused
+    // before anything else is done.
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return CSP_ECUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return CSP_ESTATE;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return CSP_ECUDA; }
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return CSP_ECUDA;

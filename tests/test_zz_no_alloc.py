@@ -133,3 +133,23 @@ def test_failed_noalloc_call_leaves_the_bound_upload_usable():
     p.launch()
     assert p.collect() == 0
     assert p.stats()["nodes"] == orc.nodes
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """On a stream being captured the call returns CSP_ESTATE at once and does nothing: the
+    capture stays valid (the graph replays what else was captured), and the next call outside
+    the capture searches as usual."""
+    p = K.Csp(I.queens(8))
+    s = torch.cuda.Stream()
+    x = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rc = K.lib().csp_solve_noalloc(p.h, K.CSP_ALL, 0, None, None, C.c_void_p(s.cuda_stream))
+        x += 1
+    assert rc == K.CSP_ESTATE
+    g.replay()
+    torch.cuda.synchronize()
+    assert x.item() == 1.0
+    rc, st, _ = _noalloc(p, K.CSP_ALL, 0)
+    assert rc == 0 and st["solutions"] == 92
