@@ -538,27 +538,22 @@ __device__ __forceinline__ uint32_t fixpoint_pair_reg(const IV<ST> &I, uint32_t 
     const uint32_t half = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
     const bool act = i < I.n;
     const int nm = (int)I.w(H_OFF_NEMASK);
+    const uint32_t done0 = done;
     uint32_t failed = 0u;
     while (pending) {
-        const uint32_t p0 = pending & 0xffffu, p1 = pending >> 16;
-        ev += (uint32_t)__popc(p0) | ((uint32_t)__popc(p1) << 16);
-        rnd += (p0 ? 1u : 0u) | (p1 ? 0x10000u : 0u);
+        rnd += ((pending & 0xffffu) ? 1u : 0u) | ((pending >> 16) ? 0x10000u : 0u);
         const int a = __ffs(d) - 1;               // the value of each fixed variable
         uint32_t rm = 0u;
         uint32_t p = pending & half;              // this lane's node (bit 16h + v)
-        // two fixed variables of each node per step; a node with none left takes a masked step
+        // one fixed variable of each node per step (a round mostly has one); a node with none
+        // left takes a masked step on its own half's first lane
         while (__any_sync(FULLMASK, p != 0u)) {
-            const bool h0 = p != 0u;
-            const int v0 = h0 ? __ffs(p) - 1 : 0;
+            const bool has = p != 0u;
+            const int v = has ? __ffs(p) - 1 : (lane & 16);
             p &= p - 1u;
-            const bool h1 = p != 0u;
-            const int v1 = h1 ? __ffs(p) - 1 : v0;
-            p &= p - 1u;
-            const int a0 = __shfl_sync(FULLMASK, a, v0);
-            const int a1 = __shfl_sync(FULLMASK, a, v1);
-            const uint2 m0 = ne_mask(I, nm, v0 & 15, i);
-            const uint2 m1 = ne_mask(I, nm, v1 & 15, i);
-            rm |= (h0 ? ne_removed(m0, a0) : 0u) | (h1 ? ne_removed(m1, a1) : 0u);
+            const int av = __shfl_sync(FULLMASK, a, v);
+            const uint2 m = ne_mask(I, nm, v & 15, i);
+            if (has) rm |= ne_removed(m, av);
         }
         d &= ~rm;
         done |= pending;
@@ -566,6 +561,9 @@ __device__ __forceinline__ uint32_t fixpoint_pair_reg(const IV<ST> &I, uint32_t 
         failed |= ((empty & 0xffffu) ? 0xffffu : 0u) | ((empty >> 16) ? 0xffff0000u : 0u);
         pending = __ballot_sync(FULLMASK, act && (d & (d - 1u)) == 0u) & ~done & ~failed;
     }
+    // each pending variable was applied once: the evaluations are the variables added to done
+    const uint32_t added = done & ~done0;
+    ev += (uint32_t)__popc(added & 0xffffu) | ((uint32_t)__popc(added >> 16) << 16);
     return failed;
 }
 
