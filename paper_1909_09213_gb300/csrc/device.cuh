@@ -503,16 +503,11 @@ __device__ __forceinline__ bool fixpoint_reg(const IV<ST> &I, uint32_t &d, uint3
         const int a = __ffs(d) - 1;               // the value of each fixed variable
         uint32_t rm = 0;
         uint32_t p = pending;
-        while (p) {                               // two fixed variables per step (independent loads)
-            const int v0 = __ffs(p) - 1;
+        while (p) {                               // one fixed variable per step (a round mostly has one)
+            const int v = __ffs(p) - 1;
             p &= p - 1;
-            const int v1 = p ? __ffs(p) - 1 : v0;
-            p &= p - 1;
-            const int a0 = __shfl_sync(FULLMASK, a, v0);
-            const int a1 = __shfl_sync(FULLMASK, a, v1);
-            const uint2 m0 = ne_mask(I, nm, v0, lane);
-            const uint2 m1 = ne_mask(I, nm, v1, lane);
-            rm |= ne_removed(m0, a0) | ne_removed(m1, a1);
+            const int av = __shfl_sync(FULLMASK, a, v);
+            rm |= ne_removed(ne_mask(I, nm, v, lane), av);
         }
         d &= ~rm;
         done |= pending;

@@ -868,7 +868,6 @@ struct Worker {
         // the parent is at its fixpoint: its fixed variables' consequences are in d already
         const uint32_t done = __ballot_sync(FULLMASK, act && (d & (d - 1u)) == 0u);
         if (i == x) d = 1u << (h ? v1 : v0);
-        __syncwarp();
         int cl;
         if (rest == 0u) {                 // the last two values: the level's slot is reused
             cl = p;
