@@ -199,11 +199,12 @@ struct Worker {
     int team;             // batch: index of the team (its queue) being helped
     int inst;             // batch: instance being searched
     int stop;             // a poll saw the stop flag
-    // register kernel: node statistics since they were last added to WarpShared, packed
-    // (nodes bits 0-7, fails 8-15, propagator evaluations 16-31, fixpoint rounds 32-47);
-    // added every 64 nodes at most, so no field overflows (a node evaluates each of its at
-    // most 32 variables once, in at most 32 rounds)
-    unsigned long long cnt;
+    // register kernel: node statistics since they were last added to WarpShared, packed in
+    // two words (nodes in the low half of cnt_nf, fails in the high half; propagator
+    // evaluations and fixpoint rounds likewise in cnt_er); added every 64 ticks (at most 128
+    // nodes), so no half overflows (a node evaluates each of its at most 32 variables once,
+    // in at most 33 rounds)
+    uint32_t cnt_nf, cnt_er;
 
     __device__ __forceinline__ WarpShared &ws() const {
         return *reinterpret_cast<WarpShared *>(&SM[wso]);
@@ -222,16 +223,27 @@ struct Worker {
     // lsm is a power of two
     __device__ __forceinline__ int slot(int k) const { return slots + (k & (lsm - 1)) * R; }
 
+    // Whether this node checks for workers owed a record: every 8th node; every node (a
+    // block's queue) or every CUBICS_HUNGRY_EVERY-th (the grid's) while workers are starved
+    // (ramp-up and the tail); never in the first nodes of a record, so that small subtrees
+    // are not passed on.  The launch's flags are read only once the register test passes.
+    __device__ __forceinline__ bool donation_due() const {
+        if (!hungry && (tick & 7u) != 0u) return false;
+        return !(SA.flags & F_NO_DONATE) &&
+               ((tick & (hungry ? (SA.batch ? 0u : CUBICS_HUNGRY_EVERY - 1u) : 7u)) == 0u) &&
+               tick - taken >= CUBICS_DONATE_AFTER;
+    }
+
     // add the packed node statistics to WarpShared (whole warp)
     __device__ __forceinline__ void fold_counts() {
-        if (lane_id() == 0 && cnt) {
+        if (lane_id() == 0 && (cnt_nf | cnt_er)) {
             WarpShared &w = ws();
-            w.nodes += cnt & 0xffull;
-            w.fails += (cnt >> 8) & 0xffull;
-            w.evals += (cnt >> 16) & 0xffffull;
-            w.rounds += cnt >> 32;
+            w.nodes += cnt_nf & 0xffffu;
+            w.fails += cnt_nf >> 16;
+            w.evals += cnt_er & 0xffffu;
+            w.rounds += cnt_er >> 16;
         }
-        cnt = 0;
+        cnt_nf = cnt_er = 0u;
     }
 
     // make the shared slot of level k (== top) free
@@ -271,7 +283,7 @@ struct Worker {
         // of a pair is two nodes)
         unsigned long long nn = 64ull;
         if constexpr (REG) {
-            nn = cnt & 0xffull;
+            nn = cnt_nf & 0xffffu;
             fold_counts();
         }
         refresh_worth();
@@ -661,10 +673,7 @@ struct Worker {
         // loads whose latency overlaps the fixpoint: stop flags and the donation signal
         const int p_stop = poll();
         uint32_t p_head = 0, p_prom = 0;
-        // every 8th node; every node while workers are starved (ramp-up and the tail); never
-        // in the first nodes of a record, so that small subtrees are not passed on
-        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? (SA.batch ? 0u : CUBICS_HUNGRY_EVERY - 1u) : 7u)) == 0u) &&
-                                tick - taken >= CUBICS_DONATE_AFTER;
+        const bool may_donate = donation_due();
         if (may_donate && lane == 0) {
             p_head = ld_volatile(&T->head);
             p_prom = ld_volatile(&T->promised);
@@ -750,8 +759,7 @@ struct Worker {
         const bool polled = full || (tick & (CUBICS_POLL_EVERY - 1u)) == 0u;
         const int p_stop = polled ? poll() : 0;
         uint32_t p_head = 0, p_prom = 0;
-        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? (SA.batch ? 0u : CUBICS_HUNGRY_EVERY - 1u) : 7u)) == 0u) &&
-                                tick - taken >= CUBICS_DONATE_AFTER;
+        const bool may_donate = donation_due();
         if (may_donate && lane == 0) {
             p_head = ld_volatile(&T->head);
             p_prom = ld_volatile(&T->promised);
@@ -771,7 +779,10 @@ struct Worker {
         if (!failed) failed = fixpoint_reg<ST>(I, d, pending, full ? 0u : done, ev, rnd);
         const bool split_root = full && !SA.batch && SA.nparts > 1;
         const bool counted = !split_root || SA.part == 0;
-        if (counted) cnt += 1ull + (failed ? 0x100ull : 0ull) + (ev << 16) + (rnd << 32);
+        if (counted) {
+            cnt_nf += failed ? 0x10001u : 1u;
+            cnt_er += (uint32_t)ev | ((uint32_t)rnd << 16);
+        }
         if (polled) stop = __shfl_sync(FULLMASK, p_stop, 0);
         if (failed) {
             refill();
@@ -882,8 +893,7 @@ struct Worker {
         const bool polled = (tick & (CUBICS_POLL_EVERY - 1u)) == 0u;
         const int p_stop = polled ? poll() : 0;
         uint32_t p_head = 0, p_prom = 0;
-        const bool may_donate = !(SA.flags & F_NO_DONATE) && ((tick & (hungry ? (SA.batch ? 0u : CUBICS_HUNGRY_EVERY - 1u) : 7u)) == 0u) &&
-                                tick - taken >= CUBICS_DONATE_AFTER;
+        const bool may_donate = donation_due();
         if (may_donate && lane == 0) {
             p_head = ld_volatile(&T->head);
             p_prom = ld_volatile(&T->promised);
@@ -892,9 +902,8 @@ struct Worker {
         uint32_t ev = 0u, rnd = 0u;
         const uint32_t fm = fixpoint_pair_reg<ST>(I, d, (1u << x) | (1u << (16 + x)), done, ev, rnd);
         const uint32_t f = (fm & 1u) | ((fm >> 15) & 2u);          // bit h: node h failed
-        cnt += 2ull + ((unsigned long long)__popc(f) << 8) +
-               ((unsigned long long)((ev & 0xffffu) + (ev >> 16)) << 16) +
-               ((unsigned long long)((rnd & 0xffffu) + (rnd >> 16)) << 32);
+        cnt_nf += 2u + ((uint32_t)__popc(f) << 16);
+        cnt_er += ((ev & 0xffffu) + (ev >> 16)) | (((rnd & 0xffffu) + (rnd >> 16)) << 16);
         if (polled) stop = __shfl_sync(FULLMASK, p_stop, 0);
         const int y = select_first_fail_pair(d, n, (f >> h) & 1u);
         const uint32_t yb = __ballot_sync(FULLMASK, i == 0 && y >= 0);
@@ -1166,7 +1175,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &Ap) {
     wk.pbin = 0;
     wk.credited = 0;
     wk.stop = 0;
-    wk.cnt = 0;
+    wk.cnt_nf = wk.cnt_er = 0u;
     wk.team = 0;
     wk.inst = 0;
     wk.init_shared();
