@@ -522,12 +522,14 @@ __device__ __forceinline__ bool fixpoint_reg(const IV<ST> &I, uint32_t &d, uint3
 // 16h + v of `pending` and `done` are node h's sets (a ballot yields both halves' sets in
 // one word), a lane shuffles from its own half and loads the offset mask of its half's
 // variable.  A half whose node failed stops at the round that emptied a domain, as
-// fixpoint_reg returns there.  Returns the failed halves (0x0000ffff: node 0, 0xffff0000:
-// node 1); evals and rounds of node h in bits 16h .. 16h + 15 of ev and rnd.
+// fixpoint_reg returns there.  The nodes are siblings: in both, x was just fixed (to ax,
+// the lane's node's value), so the first round applies x alone.  Returns the failed halves
+// (0x0000ffff: node 0, 0xffff0000: node 1); evals and rounds of node h in bits
+// 16h .. 16h + 15 of ev and rnd.
 template <bool ST>
-__device__ __forceinline__ uint32_t fixpoint_pair_reg(const IV<ST> &I, uint32_t &d,
-                                                      uint32_t pending, uint32_t done,
-                                                      uint32_t &ev, uint32_t &rnd) {
+__device__ __forceinline__ uint32_t fixpoint_pair_reg(const IV<ST> &I, uint32_t &d, int x,
+                                                      int ax, uint32_t done, uint32_t &ev,
+                                                      uint32_t &rnd) {
     const int lane = lane_id();
     const int i = lane & 15;
     const uint32_t half = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
@@ -535,6 +537,16 @@ __device__ __forceinline__ uint32_t fixpoint_pair_reg(const IV<ST> &I, uint32_t 
     const int nm = (int)I.w(H_OFF_NEMASK);
     const uint32_t done0 = done;
     uint32_t failed = 0u;
+    // the first round: x alone is pending in both nodes, fixed to ax (the lane's node's value)
+    uint32_t pending = (1u << x) | (1u << (16 + x));
+    {
+        rnd += 0x10001u;
+        d &= ~ne_removed(ne_mask(I, nm, x, i), ax);
+        done |= pending;
+        const uint32_t empty = __ballot_sync(FULLMASK, act && d == 0u);
+        failed = ((empty & 0xffffu) ? 0xffffu : 0u) | ((empty >> 16) ? 0xffff0000u : 0u);
+        pending = __ballot_sync(FULLMASK, act && (d & (d - 1u)) == 0u) & ~done & ~failed;
+    }
     while (pending) {
         rnd += ((pending & 0xffffu) ? 1u : 0u) | ((pending >> 16) ? 0x10000u : 0u);
         const int a = __ffs(d) - 1;               // the value of each fixed variable

@@ -900,7 +900,7 @@ struct Worker {
         }
         if ((tick & 63) == 0) check_limits();
         uint32_t ev = 0u, rnd = 0u;
-        const uint32_t fm = fixpoint_pair_reg<ST>(I, d, (1u << x) | (1u << (16 + x)), done, ev, rnd);
+        const uint32_t fm = fixpoint_pair_reg<ST>(I, d, x, h ? v1 : v0, done, ev, rnd);
         const uint32_t f = (fm & 1u) | ((fm >> 15) & 2u);          // bit h: node h failed
         cnt_nf += 2u + ((uint32_t)__popc(f) << 16);
         cnt_er += ((ev & 0xffffu) + (ev >> 16)) | (((rnd & 0xffffu) + (rnd >> 16)) << 16);
