@@ -488,15 +488,25 @@ __device__ __forceinline__ uint32_t ne_removed(uint2 m, int a) {
 // the child's, so re-applying them would remove nothing).  Each round applies every pending
 // variable's removals (their values are read at the start of the round: a pending variable
 // is fixed, so its domain can only become empty, which fails the node anyway), then the
-// variables newly left with one value become pending.  Returns true when some domain became
-// empty.
+// variables newly left with one value become pending.  With x >= 0 the caller states that
+// pending is {x}, just fixed to ax: the first round applies it without looking it up.
+// Returns true when some domain became empty.
 template <bool ST>
 __device__ __forceinline__ bool fixpoint_reg(const IV<ST> &I, uint32_t &d, uint32_t pending,
                                              uint32_t done, unsigned long long &evals,
-                                             unsigned long long &rounds) {
+                                             unsigned long long &rounds, int x = -1,
+                                             int ax = 0) {
     const int lane = lane_id();
     const bool act = lane < I.n;
     const int nm = (int)I.w(H_OFF_NEMASK);
+    if (x >= 0) {             // pending = {x}, just fixed to ax: the first round applies it directly
+        rounds++;
+        evals++;
+        d &= ~ne_removed(ne_mask(I, nm, x, lane), ax);
+        done |= pending;
+        if (__any_sync(FULLMASK, act && d == 0u)) return true;
+        pending = __ballot_sync(FULLMASK, act && (d & (d - 1u)) == 0u) & ~done;
+    }
     while (pending) {
         rounds++;
         evals += (unsigned)__popc(pending);

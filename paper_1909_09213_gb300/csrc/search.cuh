@@ -752,7 +752,8 @@ struct Worker {
     // variables not yet propagated, `done` the ones already propagated (full: the record's
     // root node, whose unary constraints and fixed variables are all still to apply).  On
     // success the node opens level cl in its shared slot.
-    __device__ void node_reg(uint32_t d, int cl, uint32_t pending, uint32_t done, bool full) {
+    __device__ void node_reg(uint32_t d, int cl, uint32_t pending, uint32_t done, bool full,
+                             int x = -1, int ax = 0) {
         const int lane = lane_id();
         const int n = I.n;
         tick++;
@@ -776,7 +777,7 @@ struct Worker {
             failed = __any_sync(FULLMASK, lane < n && d == 0u);
             pending = __ballot_sync(FULLMASK, lane < n && (d & (d - 1u)) == 0u);
         }
-        if (!failed) failed = fixpoint_reg<ST>(I, d, pending, full ? 0u : done, ev, rnd);
+        if (!failed) failed = fixpoint_reg<ST>(I, d, pending, full ? 0u : done, ev, rnd, x, ax);
         const bool split_root = full && !SA.batch && SA.nparts > 1;
         const bool counted = !split_root || SA.part == 0;
         if (counted) {
@@ -972,7 +973,7 @@ struct Worker {
             make_room(cl);
         }
         __syncwarp();
-        node_reg(d, cl, 1u << x, done, false);
+        node_reg(d, cl, 1u << x, done, false, x, v);
     }
 
     // child of the top level: next value of its branching variable (the level is popped
