@@ -906,11 +906,15 @@ struct Worker {
         cnt_nf += 2u + ((uint32_t)__popc(f) << 16);
         cnt_er += ((ev & 0xffffu) + (ev >> 16)) | (((rnd & 0xffffu) + (rnd >> 16)) << 16);
         if (polled) stop = __shfl_sync(FULLMASK, p_stop, 0);
-        const int y = select_first_fail_pair(d, n, (f >> h) & 1u);
-        const uint32_t yb = __ballot_sync(FULLMASK, i == 0 && y >= 0);
-        const uint32_t open = (yb & 1u) | ((yb >> 15) & 2u);       // bit h: node h branches
-        const uint32_t sol = ~f & ~open & 3u;
-        if (sol) record_solution_pair(d, sol);
+        uint32_t open = 0u;                                         // bit h: node h branches
+        int y = -1;
+        if (f != 3u) {                                              // not both failed
+            y = select_first_fail_pair(d, n, (f >> h) & 1u);
+            const uint32_t yb = __ballot_sync(FULLMASK, i == 0 && y >= 0);
+            open = (yb & 1u) | ((yb >> 15) & 2u);
+            const uint32_t sol = ~f & ~open & 3u;
+            if (sol) record_solution_pair(d, sol);
+        }
         if (open) {
             // node 1's level first (at cl, which has room), node 0's above it
             const int l0 = (open & 2u) ? cl + 1 : cl;
