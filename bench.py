@@ -329,8 +329,19 @@ class Queens:
             g["nodes"], g["fails"], g["solutions"], g["hash_sum"], g["hash_xor"])
 
     def extra(self, K, st):
-        return {"solutions_per_step": st["solutions"],
-                "time_to_all_solutions_ms": st["ms"]}
+        """untimed: the autotuner's shapes for this problem (warps per block x two nodes or
+        one node per warp x the problem's own or a twice wider bitset) with their nodes/s"""
+        from paper_1909_09213_gb300 import tune
+        out = {"solutions_per_step": st["solutions"],
+               "time_to_all_solutions_ms": st["ms"]}
+        t, entry = tune.tune_single(self.model, reps=1, use_cache=False)
+        name = lambda c: (f"warps{c['warps_per_block']}/"
+                          f"{'two_nodes' if c['threads_per_node'] == 16 else 'one_node'}_per_warp/"
+                          f"words{c['domain_words'] or 1}")
+        out["tuned_shape"] = name(entry["tiling"])
+        out["shape_nodes_per_s"] = {name(c): round(st["nodes"] / (ms * 1e-3))
+                                    for ms, c in entry["candidates"]}
+        return out
 
     def oracle_sample(self, depth):
         """The subtree under x0=0, x1=2 (, x2=4): a bounded piece of the same search."""

@@ -95,6 +95,15 @@ typedef struct {
                                  tree.  Same counts and hashes either way; no effect on
                                  first-solution search, partitions, the learned brancher
                                  (CSP_BR_LEARNED) or csp_solve_noalloc */
+    int32_t domain_words;     /* search bitset width: 0 = the problem's own (csp_layout's W);
+                                 1, 2, 4 or 8 words per domain, at least the problem's own:
+                                 the search runs with wider domains (the same values, upper
+                                 words empty), the autotuner's width axis.  The register-held
+                                 kernel and two nodes per warp need one-word domains, so
+                                 threads_per_node = 16 with a wider width is CSP_EINVAL.
+                                 csp_propagate, csp_root_domains and csp_layout keep the
+                                 problem's own width.  A batch runs at the widest width of its
+                                 problems: any other nonzero value is CSP_EINVAL there */
 } csp_tiling;
 
 typedef struct {

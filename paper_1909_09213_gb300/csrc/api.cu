@@ -172,6 +172,7 @@ struct Plan {
     Shape shape;
     int R = 0, depth = 0;
     int pairs = 0;                   // two sibling nodes per warp (register kernel)
+    int W = 1;                       // words per domain of the search (csp_tiling.domain_words)
     size_t o_inst = 0, o_off = 0, o_g = 0, o_team = 0, o_qseq = 0, o_qrec = 0, o_spill = 0,
            o_sols = 0, o_mlp_params = 0, o_mlp_packed = 0;
     // all-solution search split at depth k into units solved by per-block teams
@@ -450,7 +451,10 @@ int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<ui
                 bool allow_split = true) {
     std::vector<uint32_t> local;
     std::vector<uint32_t> &B = blk ? *blk : local;
-    encode(h, h->W, B);
+    // a search may run with wider domains than the problem's own (the tuner's width axis);
+    // propagation keeps the problem's layout
+    const int W = mode == CSP_PROPAGATE ? h->W : std::max(h->W, (int)h->tiling.domain_words);
+    encode(h, W, B);
     Plan p;
     Carver c;
     p.o_inst = c.take(B.size() * 4);
@@ -464,7 +468,7 @@ int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<ui
         *P = p;
         return CSP_OK;
     }
-    const int R = record_words(h->n * h->W, h->W);
+    const int R = record_words(h->n * W, W);
     const bool learned = h->brancher == CSP_BR_LEARNED;
     const int pairs = pairs_of(h->tiling, (B[H_FLAGS] & FLAG_NE_REG) != 0 && !learned, h->n,
                                mode == CSP_ALL);
@@ -474,16 +478,17 @@ int plan_single(const csp *h, int32_t mode, int64_t cap, Plan *P, std::vector<ui
     // searches the whole tree with one shared queue
     p.split = allow_split && mode == CSP_ALL && split_depth_of(h->tiling) > 0 && h->nparts == 1 &&
               !learned;
-    int rc = make_shape(h->tiling, h->W, R, depth, (int)B[H_CONS_WORDS], p.split, learned, false,
+    int rc = make_shape(h->tiling, W, R, depth, (int)B[H_CONS_WORDS], p.split, learned, false,
                         h->n, (int)B[H_N_TAB], (B[H_FLAGS] & FLAG_NE_REG) != 0, &p.shape);
     if (rc) return rc;
     const Shape &s = p.shape;
     p.R = R;
     p.depth = depth;
     p.pairs = pairs;
+    p.W = W;
     if (p.split) {
         // per-block teams (one queue each) over the units, the level buffers and the units
-        const size_t S4 = (size_t)h->n * h->W * 4;
+        const size_t S4 = (size_t)h->n * W * 4;
         p.ucap = std::max<int64_t>(1024, std::min<int64_t>(1 << 16, (int64_t)((32u << 20) / S4)));
         p.o_off = c.take((size_t)(2 * p.ucap) * 8);              // zero block offsets
         p.o_g = c.take(sizeof(GState));
@@ -768,13 +773,15 @@ int csp_layout(const csp_t *h, int32_t *n, int32_t *W, int32_t *lo0) {
 // queue capacity a power of two; threads per node 0 or a multiple of 32 up to 1024
 static bool tiling_ok(const csp_tiling &t) {
     const int tp = t.threads_per_node;
+    const int dw = t.domain_words;
     return !(t.queue_records & (t.queue_records - 1)) && tp >= 0 && tp <= 1024 &&
-           (tp % 32 == 0 || tp == 16) && t.split_depth >= -1 && t.split_depth <= 8;
+           (tp % 32 == 0 || tp == 16) && t.split_depth >= -1 && t.split_depth <= 8 &&
+           (dw == 0 || dw == 1 || dw == 2 || dw == 4 || dw == 8);
 }
 
 int csp_set_tiling(csp_t *h, const csp_tiling *t) {
     if (!h) return CSP_EINVAL;
-    const csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0, 0, 0};
+    const csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0, 0, 0, 0};
     if (!tiling_ok(nt)) return CSP_EINVAL;
     h->tiling = nt;
     invalidate(h);
@@ -885,7 +892,7 @@ static cudaError_t split_launch(csp *h, const csp_limits *lim) {
     const Plan &P = h->plan;
     const cudaStream_t st = h->stream;
     uint8_t *w = h->ws;
-    const int n = h->n, W = h->W, S = n * W;
+    const int n = h->n, W = P.W, S = n * W;
     const size_t S4 = (size_t)S * 4;
     const uint32_t *blk = (const uint32_t *)(w + P.o_inst);
     uint8_t *A = w + P.o_A, *Bf = w + P.o_B;
@@ -991,7 +998,7 @@ int csp_launch(csp_t *h, const csp_limits *lim) {
     if (e == cudaSuccess) e = launch_init_single(A, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess)
-        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.kind, A, P.shape.blocks,
+        e = launch_search(P.W, P.shape.stage_words > 0, P.shape.kind, A, P.shape.blocks,
                           P.shape.warps * 32, P.shape.smem, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
     h->stats.workers = P.shape.blocks * P.shape.warps;
@@ -1333,8 +1340,9 @@ int csp_batch_create_roots(csp_batch_t **out, csp_t *base, int32_t count, const 
 
 int csp_batch_set_tiling(csp_batch_t *b, const csp_tiling *t) {
     if (!b) return CSP_EINVAL;
-    csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0, 0, 0};
+    csp_tiling nt = t ? *t : csp_tiling{0, 0, 0, 0, 0, 0, 0};
     if (!tiling_ok(nt)) return CSP_EINVAL;
+    if (nt.domain_words != 0 && nt.domain_words != b->W) return CSP_EINVAL;   // arena encoded at b->W
     b->tiling = nt;
     b->uploaded = false;
     drop_graph(b);
@@ -1601,7 +1609,7 @@ int csp_solve_noalloc(csp_t *h, int32_t mode, int64_t cap, int32_t *sol_out,
     if (e == cudaSuccess) e = cudaMemsetAsync(ws + P.o_team, 0, sizeof(Team), st);
     if (e == cudaSuccess) e = launch_init_single(A, st);
     if (e == cudaSuccess)
-        e = launch_search(h->W, P.shape.stage_words > 0, P.shape.kind, A, P.shape.blocks,
+        e = launch_search(P.W, P.shape.stage_words > 0, P.shape.kind, A, P.shape.blocks,
                           P.shape.warps * 32, P.shape.smem, st);
     GState g;
     if (e == cudaSuccess)

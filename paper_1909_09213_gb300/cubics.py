@@ -35,7 +35,8 @@ class csp_limits(C.Structure):
 class csp_tiling(C.Structure):
     _fields_ = [("blocks", C.c_int32), ("warps_per_block", C.c_int32),
                 ("smem_levels", C.c_int32), ("queue_records", C.c_int32),
-                ("threads_per_node", C.c_int32), ("split_depth", C.c_int32)]
+                ("threads_per_node", C.c_int32), ("split_depth", C.c_int32),
+                ("domain_words", C.c_int32)]
 
 
 class csp_stats_t(C.Structure):
@@ -150,9 +151,9 @@ def limits(node_limit=0, time_limit_ns=0, wait_limit_ns=0, flags=0) -> csp_limit
 
 
 def tiling(blocks=0, warps_per_block=0, smem_levels=0, queue_records=0,
-           threads_per_node=0, split_depth=0) -> csp_tiling:
+           threads_per_node=0, split_depth=0, domain_words=0) -> csp_tiling:
     return csp_tiling(blocks, warps_per_block, smem_levels, queue_records, threads_per_node,
-                      split_depth)
+                      split_depth, domain_words)
 
 
 def _stats_dict(s: csp_stats_t) -> dict:

@@ -5,9 +5,10 @@ memory grows) becomes a measured choice: warps per block (workers sharing one in
 staged constraints and one work queue), search levels kept in shared memory per worker, and
 queue capacity.  Candidates are timed on a calibration subset with CUDA events (the
 library's own launch timing); the fastest is cached in a JSON file keyed by GPU, domain
-width and a size bucket.  For propagation alone the tuned axis is the number of threads
-per node: a warp per domain state, or a whole block per state (tune_propagate).  A tiling
-changes only speed, never results.
+width and a size bucket.  For one problem's search the axes are warps per block, threads
+per node (two sibling nodes per warp or one) and the bitset width (the problem's own or
+wider); for propagation alone the number of threads per node: a warp per domain state, or
+a whole block per state (tune_propagate).  A tiling changes only speed, never results.
 """
 from __future__ import annotations
 
@@ -53,7 +54,13 @@ BATCH_CANDIDATES = [
     dict(warps_per_block=w, smem_levels=l)
     for w in (1, 2, 4, 8) for l in (8, 24)
 ]
-SINGLE_CANDIDATES = [dict(warps_per_block=w) for w in (4, 8, 16)]
+def single_candidates(model):
+    """Warps per block x threads per node (16: two sibling nodes per warp, where the problem
+    allows it; 32: one node per warp) x bitset width (the problem's own, and twice that)."""
+    W = K.Csp(model).layout()[1]
+    widths = [0] + ([2 * W] if 2 * W <= 8 else [])
+    return [dict(warps_per_block=w, threads_per_node=t, domain_words=dw)
+            for w in (4, 8, 16) for t in (16, 32) for dw in widths]
 
 
 def tune_batch(models, mode=K.CSP_FIRST, calib=256, reps=2, use_cache=True, verbose=False):
@@ -89,19 +96,23 @@ def tune_batch(models, mode=K.CSP_FIRST, calib=256, reps=2, use_cache=True, verb
 
 
 def tune_single(model, mode=K.CSP_ALL, reps=2, use_cache=True, verbose=False):
-    """Best csp_tiling for one problem, timed on the problem itself."""
+    """Best csp_tiling for one problem, timed on the problem itself (the search's device
+    time); shapes the problem does not admit (CSP_EINVAL) are skipped."""
     key = f"{_gpu_name()}|single|{mode}|{size_bucket([model])}|{model.name}"
     cache = _load() if use_cache else {}
     if key in cache:
         return K.tiling(**cache[key]["tiling"]), cache[key]
     results = []
-    for cand in SINGLE_CANDIDATES:
+    for cand in single_candidates(model):
         p = K.Csp(model)
         p.set_tiling(K.tiling(**cand))
         best = None
-        for _ in range(reps + 1):
-            rc, st, _ = p.solve(mode, 0)
-            best = st["ms"] if best is None else min(best, st["ms"])
+        try:
+            for _ in range(reps + 1):
+                rc, st, _ = p.solve(mode, 0)
+                best = st["ms"] if best is None else min(best, st["ms"])
+        except K.CspError:
+            continue
         results.append((best, cand))
         if verbose:
             print(f"tune single {cand}: {best:.2f} ms", flush=True)

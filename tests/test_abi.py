@@ -120,6 +120,33 @@ def test_two_nodes_per_warp_planning():
         p.set_tiling(K.tiling(threads_per_node=8))
 
 
+def test_wider_domain_words_planning():
+    """csp_tiling.domain_words: a search planned at a wider bitset has wider records (a larger
+    workspace); widths that are not 1, 2, 4 or 8 are refused; two nodes per warp need one-word
+    domains; a batch takes only its own width."""
+    p = K.Csp(I.queens(8))
+    base = None
+    for dw in (0, 1, 2, 4, 8):
+        p.set_tiling(K.tiling(blocks=2, warps_per_block=4, split_depth=-1, domain_words=dw))
+        b = p.workspace_bytes(K.CSP_ALL, 0)
+        if dw in (0, 1):
+            base = b if base is None else base
+            assert b == base
+        else:
+            assert b > base
+    assert p.layout()[1] == 1                    # the problem's own layout is unchanged
+    p.set_tiling(K.tiling(blocks=2, threads_per_node=16, domain_words=2))
+    with pytest.raises(K.CspError) as e:
+        p.workspace_bytes(K.CSP_ALL, 0)
+    assert e.value.code == K.CSP_EINVAL
+    L = K.lib()
+    for bad in (3, 5, 16, -1):
+        assert L.csp_set_tiling(p.h, C.byref(K.tiling(domain_words=bad))) == K.CSP_EINVAL
+    bt = K.Batch([K.Csp(I.queens(6)), K.Csp(I.queens(7))])
+    assert L.csp_batch_set_tiling(bt.b, C.byref(K.tiling(domain_words=2))) == K.CSP_EINVAL
+    assert L.csp_batch_set_tiling(bt.b, C.byref(K.tiling(domain_words=1))) == 0
+
+
 def test_models_build_through_the_abi():
     for m in [I.queens(8), I.worked_example("lin", "table"), I.model_rb(1, 20, 8),
               I.lin_alldiff(3), I.random_tiny(5)]:

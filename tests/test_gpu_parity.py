@@ -320,6 +320,44 @@ def test_two_nodes_per_warp(tname):
     assert compared >= 15
 
 
+@pytest.mark.parametrize("dw", [2, 4, 8])
+def test_search_at_wider_domain_words(dw):
+    """csp_tiling.domain_words: the same searches with wider bitsets (upper words empty) give
+    the oracle's counts, hashes and stored solutions; propagation keeps the problem's layout
+    and fixpoints."""
+    models = [I.queens(8), random_ne_model(9500, 12, 6, 30),
+              I.model_rb(I.seed_for(I.CFG_RB, 77), 14, 7), I.worked_example("lin", "table"),
+              mixed_model(120, 30, 5), strided_queens(7, 13)]
+    for m in models:
+        if K.Csp(m).layout()[1] > dw:
+            continue
+        search_parity(m, K.tiling(domain_words=dw), cap=2000)
+        search_parity(m, K.tiling(domain_words=dw, split_depth=-1), cap=2000)
+    p = K.Csp(I.queens(10))
+    root = p.root_domains().reshape(1, -1)
+    out0, f0 = p.propagate(root)
+    p.set_tiling(K.tiling(domain_words=dw))
+    out1, f1 = p.propagate(root)
+    assert np.array_equal(out0, out1) and np.array_equal(f0, f1)
+
+
+def test_tuned_single_shape_keeps_the_results():
+    """The autotuner's axes for one problem (warps per block, two nodes or one per warp, the
+    problem's own or a wider bitset): every shape it times gives the oracle's counts, and so
+    does the shape it picks.  Two nodes per warp need one-word domains, so they are tried at
+    the problem's own width only."""
+    from paper_1909_09213_gb300 import tune
+    m = I.queens(10)
+    t, entry = tune.tune_single(m, reps=0, use_cache=False)
+    tried = {(c["threads_per_node"], c["domain_words"]) for _, c in entry["candidates"]}
+    assert tried == {(16, 0), (32, 0), (32, 2)}
+    search_parity(m, t)
+    m2 = I.model_rb(I.seed_for(I.CFG_RB, 78), 20, 8)            # tables: one node per warp
+    t2, entry2 = tune.tune_single(m2, reps=0, use_cache=False)
+    assert all(c["threads_per_node"] == 32 for _, c in entry2["candidates"])
+    search_parity(m2, t2)
+
+
 def test_two_nodes_per_warp_limits_and_modes():
     p = K.Csp(I.queens(12))
     p.set_tiling(K.tiling(threads_per_node=16, blocks=2, warps_per_block=2, split_depth=-1))
