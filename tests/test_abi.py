@@ -168,3 +168,23 @@ def test_encoded_root_domains_equal_the_oracle_domains():
         om = O.OracleModel(m)
         want = flags_to_bits(om, om.root_flags(), n, W, lo0).reshape(n, W)
         assert np.array_equal(p.root_domains(), want), m.name
+
+
+def test_tuner_candidates_for_one_problem():
+    """The autotuner's search shapes (host side, no device): warps per block x two nodes or
+    one per warp x the problem's own bitset width or twice it, the wider width only while it
+    is at most 8 words."""
+    from paper_1909_09213_gb300 import tune
+    one = tune.single_candidates(I.queens(8))                   # one word per domain
+    assert len(one) == 3 * 2 * 2
+    assert {c["domain_words"] for c in one} == {0, 2}
+    assert {c["threads_per_node"] for c in one} == {16, 32}
+    assert {c["warps_per_block"] for c in one} == {4, 8, 16}
+    m = I.CspModel(n=3, lo=[0, 0, 0], hi=[200, 200, 200], name="wide")   # 201 values: 8 words
+    m.ne.append((0, 1, 0))
+    assert K.Csp(m).layout()[1] == 8
+    wide = tune.single_candidates(m)
+    assert {c["domain_words"] for c in wide} == {0} and len(wide) == 6
+    for c in one + wide:                                     # every candidate is a valid tiling
+        p = K.Csp(I.queens(8))
+        p.set_tiling(K.tiling(**c))
